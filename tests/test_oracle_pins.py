@@ -1,0 +1,343 @@
+"""Pins of the FP64 CPU oracle against facts the paper and mathematics fix.
+
+Each test checks the oracle against something other than itself: closed
+forms (plane-wave symbols of the stencils, the Hartree cosine, Gaussian
+integrals), textbook or library routines built independently (explicit DFT
+matrices, numpy QR, scipy sparse eigensolvers), brute-force finite
+differences, and invariants of the method (Sec. 2-3 of the paper).
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from oracle import pou_oracle as O
+from paper_1510_07230_gb300 import inputs
+
+
+def _plane(cfg, m, phase=0.0):
+    x, y, z = O.grid_coords(cfg)
+    Lx, Ly, Lz = cfg.L
+    arg = (2 * math.pi * m[0] * x[None, None, :] / Lx + 2 * math.pi * m[1] * y[None, :, None] / Ly
+           + 2 * math.pi * m[2] * z[:, None, None] / Lz)
+    return np.cos(arg + phase)
+
+
+def _symbol(order, m, n, h):
+    """Eigenvalue of -Lap_h on exp(2 pi i m x / L) for one axis (Fourier analysis)."""
+    th = 2 * math.pi * m / n
+    if order == 2:
+        return 4.0 * math.sin(th / 2) ** 2 / h ** 2
+    return (30.0 - 32.0 * math.cos(th) + 2.0 * math.cos(2 * th)) / (12.0 * h ** 2)
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_laplacian_plane_wave_symbol(order):
+    cfg = O.Config(n=(12, 10, 9), L=(6.0, 5.5, 4.0), order=order)
+    for m in [(1, 0, 0), (0, 2, 0), (3, 1, 4), (6, 5, 4)]:
+        u = _plane(cfg, m, 0.3)
+        lam = sum(_symbol(order, m[a], cfg.n[a], cfg.h[a]) for a in range(3))
+        np.testing.assert_allclose(-O.laplacian(u, cfg), lam * u, atol=1e-10 * lam)
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_lambda_max_brute_force(order):
+    cfg = O.Config(n=(4, 5, 3), L=(2.0, 2.5, 1.5), order=order)
+    Ng = cfg.Ng
+    A = np.zeros((Ng, Ng))
+    for k in range(Ng):
+        e = np.zeros(Ng)
+        e[k] = 1.0
+        A[:, k] = (-0.5 * O.laplacian(e.reshape(cfg.shape), cfg)).ravel()
+    lam = np.linalg.eigvalsh(0.5 * (A + A.T))
+    # max over all discrete modes of the closed-form symbol
+    best = max(0.5 * sum(_symbol(order, m[a], cfg.n[a], cfg.h[a]) for a in range(3))
+               for m in itertools.product(*(range(v) for v in cfg.n)))
+    assert abs(lam[-1] - best) < 1e-10 * best
+    # lambda_max_kinetic is the Nyquist value, an upper bound reached for even n
+    assert O.lambda_max_kinetic(cfg) >= lam[-1] - 1e-9
+
+
+def test_vext_single_well_closed_form():
+    L, n, w = 16.0, 32, 0.8
+    cfg = O.cubic(n, L)
+    R = np.array([[8.0, 8.0, 8.0]])
+    V = O.vext_gaussians(cfg, R, np.array([3.0]), w)
+    x, y, z = O.grid_coords(cfg)
+    d2 = (z[:, None, None] - 8) ** 2 + (y[None, :, None] - 8) ** 2 + (x[None, None, :] - 8) ** 2
+    np.testing.assert_allclose(V, -3.0 * np.exp(-d2 / (2 * w * w)), atol=1e-14)
+    # integral of a Gaussian: -Z (2 pi w^2)^(3/2); the periodic trapezoid rule is exact here
+    assert abs(cfg.dV * V.sum() + 3.0 * (2 * math.pi * w * w) ** 1.5) < 1e-10
+
+
+def test_vext_periodic_images():
+    cfg = O.Config(n=(20, 16, 12), L=(8.0, 7.0, 6.0))
+    R = np.array([[0.1, 6.9, 3.0], [4.0, 0.2, 5.9]])
+    Z = np.array([2.0, 5.0])
+    V1 = O.vext_gaussians(cfg, R, Z, 0.8)
+    V2 = O.vext_gaussians(cfg, R + np.array([[8.0, -7.0, 6.0], [-8.0, 7.0, -6.0]]), Z, 0.8)
+    # shifting an atom by one box length changes only which images are summed (all ~1e-10 level)
+    np.testing.assert_allclose(V1, V2, atol=1e-9)
+    # integral: -sum Z (2 pi w^2)^(3/2), up to the far images not summed
+    assert abs(cfg.dV * V1.sum() + Z.sum() * (2 * math.pi * 0.64) ** 1.5) < 1e-6
+
+
+def test_hartree_cosine_closed_form():
+    cfg = O.Config(n=(16, 12, 10), L=(7.0, 6.0, 5.0))
+    x, y, z = O.grid_coords(cfg)
+    A, rbar = 0.3, 1.1
+    for axis, coord, Lax in ((0, x[None, None, :], 7.0), (1, y[None, :, None], 6.0), (2, z[:, None, None], 5.0)):
+        rho = rbar + A * np.cos(2 * math.pi * coord / Lax) + 0 * np.zeros(cfg.shape)
+        VH = O.hartree_potential(rho, cfg)
+        exact = A * Lax ** 2 / math.pi * np.cos(2 * math.pi * coord / Lax) + 0 * np.zeros(cfg.shape)
+        np.testing.assert_allclose(VH, exact, atol=1e-12)
+        EH = 0.5 * cfg.dV * np.sum(rho * VH)
+        vol = 7.0 * 6.0 * 5.0
+        assert abs(EH - A * A * Lax ** 2 * vol / (4 * math.pi)) < 1e-10
+    # constant density: neutralising background gives V_H = 0
+    assert np.max(np.abs(O.hartree_potential(np.full(cfg.shape, 2.5), cfg))) < 1e-13
+
+
+def test_hartree_against_explicit_dft_matrices():
+    cfg = O.Config(n=(4, 3, 5), L=(3.0, 2.0, 4.0))
+    rng = np.random.default_rng(0)
+    rho = rng.uniform(0, 1, cfg.shape)
+
+    def dft(n):
+        j = np.arange(n)
+        return np.exp(-2j * math.pi * np.outer(j, j) / n)
+
+    nx, ny, nz = cfg.n
+    Fx, Fy, Fz = dft(nx), dft(ny), dft(nz)
+    rh = np.einsum("az,by,cx,zyx->abc", Fz, Fy, Fx, rho)
+    # |G|^2 with m folded to the symmetric range (|m| = n/2 at Nyquist)
+    def g(n, L):
+        m = np.array([k if k <= n // 2 else k - n for k in range(n)], dtype=float)
+        return 2 * math.pi * m / L
+    gx, gy, gz = g(nx, 3.0), g(ny, 2.0), g(nz, 4.0)
+    G2 = gz[:, None, None] ** 2 + gy[None, :, None] ** 2 + gx[None, None, :] ** 2
+    K = np.where(G2 > 0, 4 * math.pi / np.where(G2 > 0, G2, 1), 0.0)
+    vh = np.einsum("za,yb,xc,abc->zyx", np.conj(Fz), np.conj(Fy), np.conj(Fx), rh * K).real / cfg.Ng
+    np.testing.assert_allclose(O.hartree_potential(rho, cfg), vh, atol=1e-12)
+
+
+def test_exchange_closed_form_and_derivative():
+    assert abs(O.exchange_energy_density(np.array(1.0)) + 0.75 * (3 / math.pi) ** (1 / 3)) < 1e-15
+    rho = np.array([1e-3, 0.05, 0.7, 3.0])
+    eps = 1e-6 * rho
+    fd = (O.exchange_energy_density(rho + eps) - O.exchange_energy_density(rho - eps)) / (2 * eps)
+    np.testing.assert_allclose(O.exchange_potential(rho), fd, rtol=1e-8)
+    assert O.exchange_potential(np.array(0.0)) == 0.0
+
+
+def test_cholesky_qr_matches_numpy_qr():
+    cfg = O.Config(n=(6, 5, 4), L=(3.0, 2.5, 2.0), N=5)
+    U = inputs.random_orbitals(3, 5, cfg.n)
+    W, S, R = O.cholesky_qr(U, cfg)
+    X = math.sqrt(cfg.dV) * U.reshape(5, -1).T  # columns = orbitals, unit-weight inner product
+    Qm, Rm = np.linalg.qr(X)
+    sgn = np.sign(np.diag(Rm))
+    Qm, Rm = Qm * sgn[None, :], Rm * sgn[:, None]
+    np.testing.assert_allclose(W.reshape(5, -1).T * math.sqrt(cfg.dV), Qm, atol=1e-12)
+    np.testing.assert_allclose(R, Rm, rtol=1e-12, atol=1e-12)
+    assert np.max(np.abs(O.inner_matrix(W, W, cfg) - np.eye(5))) < 1e-12
+
+
+def test_energy_plane_wave_and_rotation_invariance():
+    cfg = O.cubic(8, 5.0, N=1, hartree=0, exchange=0)
+    u = _plane(cfg, (1, 0, 0))
+    u /= math.sqrt(cfg.dV * np.sum(u * u))
+    e = O.energy(u[None], np.zeros(cfg.shape), cfg)
+    lam = 0.5 * _symbol(2, 1, 8, cfg.h[0])
+    assert abs(e - 2 * lam) < 1e-12
+    # E(UP) = E(U) for orthogonal P (Sec. 2.2), interacting case
+    cfg2 = O.cubic(8, 6.0, N=3)
+    R, Z = inputs.atoms(5, 2, 6.0, "const4")
+    vext = O.vext_gaussians(cfg2, R, Z, 0.8)
+    W, _, _ = O.cholesky_qr(inputs.random_orbitals(5, 3, cfg2.n), cfg2)
+    P, _ = np.linalg.qr(np.random.default_rng(1).standard_normal((3, 3)))
+    WP = (P.T @ W.reshape(3, -1)).reshape(W.shape)
+    assert abs(O.energy(W, vext, cfg2) - O.energy(WP, vext, cfg2)) < 1e-11
+    assert abs(cfg2.dV * O.density(W).sum() - 2 * 3) < 1e-11
+
+
+def _free_levels(cfg, N):
+    lv = sorted(0.5 * sum(_symbol(cfg.order, m[a], cfg.n[a], cfg.h[a]) for a in range(3))
+                for m in itertools.product(*(range(v) for v in cfg.n)))
+    return lv[:N]
+
+
+@pytest.mark.parametrize("order,N", [(2, 1), (2, 7), (4, 7)])
+def test_free_particle_closed_shells(order, N):
+    cfg = O.cubic(8, 6.0, order=order, N=N, hartree=0, exchange=0)
+    vext = np.zeros(cfg.shape)
+    U0 = inputs.random_orbitals(11, N, cfg.n)
+    st = O.run(U0, vext, cfg, 600, e_tol=1e-15)
+    exact = 2.0 * sum(_free_levels(cfg, N))
+    assert abs(st.E - exact) < 1e-9 * max(1.0, abs(exact))
+
+
+@pytest.mark.parametrize("N", [1, 7])
+def test_jellium_with_exchange(N):
+    L = 6.0
+    cfg = O.cubic(8, L, order=2, N=N, hartree=1, exchange=1)
+    st = O.run(inputs.random_orbitals(12, N, cfg.n), np.zeros(cfg.shape), cfg, 800, e_tol=1e-15)
+    rbar = 2.0 * N / L ** 3
+    ex = -0.75 * (3 / math.pi) ** (1 / 3) * rbar ** (4 / 3) * L ** 3
+    exact = 2.0 * sum(_free_levels(cfg, N)) + ex
+    assert abs(st.E - exact) < 1e-8
+    assert np.max(np.abs(st.rho - rbar)) < 1e-5
+
+
+def _sparse_h(cfg, vext):
+    """FD Hamiltonian built from 1-D periodic difference matrices by Kronecker sums."""
+    def d2(n, h, order):
+        if order == 2:
+            c = {0: -2.0, 1: 1.0, -1: 1.0}
+            s = 1.0 / h ** 2
+        else:
+            c = {0: -30.0, 1: 16.0, -1: 16.0, 2: -1.0, -2: -1.0}
+            s = 1.0 / (12 * h ** 2)
+        M = np.zeros((n, n))
+        for i in range(n):
+            for k, v in c.items():
+                M[i, (i + k) % n] += v * s
+        return sp.csr_matrix(M)
+    nx, ny, nz = cfg.n
+    hx, hy, hz = cfg.h
+    Ix, Iy, Iz = sp.identity(nx), sp.identity(ny), sp.identity(nz)
+    lap = (sp.kron(sp.kron(Iz, Iy), d2(nx, hx, cfg.order))
+           + sp.kron(sp.kron(Iz, d2(ny, hy, cfg.order)), Ix)
+           + sp.kron(sp.kron(d2(nz, hz, cfg.order), Iy), Ix))
+    return (-0.5 * lap + sp.diags(vext.ravel())).tocsr()
+
+
+@pytest.mark.parametrize("order,N", [(2, 1), (2, 4), (4, 3)])
+def test_noninteracting_well_vs_eigsh(order, N):
+    cfg = O.cubic(12, 8.0, order=order, N=N, hartree=0, exchange=0)
+    R = np.array([[3.1, 4.2, 3.7], [5.3, 3.5, 4.9]])
+    vext = O.vext_gaussians(cfg, R, np.array([4.0, 3.0]), 0.8)
+    ev = spla.eigsh(_sparse_h(cfg, vext), k=N + 2, which="SA", tol=1e-13)[0]
+    exact = 2.0 * np.sort(ev)[:N].sum()
+    st = O.run(inputs.random_orbitals(13, N, cfg.n), vext, cfg, 2000, e_tol=1e-16)
+    assert abs(st.E - exact) < 1e-8
+
+
+def test_self_consistency_subspace():
+    cfg = O.cubic(8, 6.0, order=2, N=3)
+    R, Z = inputs.atoms(21, 2, 6.0, "const4")
+    Z = np.array([3.0, 3.0])
+    vext = O.vext_gaussians(cfg, R, Z, 0.8)
+    st = O.run(inputs.random_orbitals(21, 3, cfg.n), vext, cfg, 3000, e_tol=1e-16)
+    H = _sparse_h(cfg, st.V).toarray()
+    lam, vec = np.linalg.eigh(H)
+    Pv = vec[:, :3]  # lowest three eigenvectors, unit Euclidean norm
+    Wn = st.W.reshape(3, -1).T * math.sqrt(cfg.dV)
+    s = np.linalg.svd(Pv.T @ Wn, compute_uv=False)
+    assert np.min(s) > 1 - 1e-10  # cos of the largest principal angle
+    assert lam[2] < lam[3] - 1e-3  # the occupied subspace is well separated
+
+
+def test_orbital_gradient_finite_differences():
+    cfg = O.Config(n=(6, 5, 6), L=(4.0, 3.5, 4.5), order=4, N=2)
+    R = np.array([[1.0, 1.2, 2.0], [3.0, 2.5, 0.7]])
+    vext = O.vext_gaussians(cfg, R, np.array([2.0, 4.0]), 0.8)
+    U = 0.3 * inputs.random_orbitals(7, 2, cfg.n)
+    g = O.energy_gradient_orbitals(U, vext, cfg)
+    rng = np.random.default_rng(2)
+    idx = [tuple(rng.integers(0, s) for s in U.shape) for _ in range(25)]
+    eps = 1e-5
+    for ix in idx:
+        Up, Um = U.copy(), U.copy()
+        Up[ix] += eps
+        Um[ix] -= eps
+        fd = (O.energy(Up, vext, cfg) - O.energy(Um, vext, cfg)) / (2 * eps)
+        assert abs(fd - g[ix]) <= 1e-7 * max(1.0, np.max(np.abs(g))) , (ix, fd, g[ix])
+
+
+def test_atom_gradient_finite_differences():
+    cfg = O.Config(n=(10, 9, 8), L=(5.0, 4.5, 4.0), order=2, N=2)
+    R = np.array([[1.0, 1.2, 2.0], [3.9, 2.5, 0.3]])
+    Z = np.array([2.0, 4.0])
+    U = inputs.random_orbitals(8, 2, cfg.n)
+    U, _, _ = O.cholesky_qr(U, cfg)
+    dR, dZ = O.energy_gradient_atoms(U, cfg, R, Z, 0.8)
+    eps = 1e-5
+
+    def E(Rv, Zv):
+        return O.energy(U, O.vext_gaussians(cfg, Rv, Zv, 0.8), cfg)
+    for I in range(2):
+        for a in range(3):
+            Rp, Rm = R.copy(), R.copy()
+            Rp[I, a] += eps
+            Rm[I, a] -= eps
+            fd = (E(Rp, Z) - E(Rm, Z)) / (2 * eps)
+            assert abs(fd - dR[I, a]) < 1e-8 * max(1.0, abs(fd))
+        Zp, Zm = Z.copy(), Z.copy()
+        Zp[I] += eps
+        Zm[I] -= eps
+        fd = (E(R, Zp) - E(R, Zm)) / (2 * eps)
+        assert abs(fd - dZ[I]) < 1e-8 * max(1.0, abs(fd))
+
+
+def test_invariants_along_trajectory():
+    cfg = O.cubic(10, 7.0, order=2, N=4)
+    R, Z = inputs.atoms(31, 2, 7.0, "const4")
+    vext = O.vext_gaussians(cfg, R, Z, 0.8)
+    st = O.initial_state(inputs.random_orbitals(31, 4, cfg.n), vext, cfg)
+    for _ in range(60):
+        C, Q = st.C, st.Q
+        O.iterate(st, vext, cfg)
+        rec = st.history[-1]
+        assert np.max(np.abs(O.inner_matrix(st.W, st.W, cfg) - np.eye(4))) < 1e-12
+        assert abs(cfg.dV * st.rho.sum() - 8.0) < 1e-10
+        if not rec.forced:
+            assert rec.energy <= C - cfg.rho1 * rec.tau * rec.znorm2 + 1e-12
+        assert st.Q == pytest.approx(cfg.eta * Q + 1)
+
+
+def test_monotone_when_eta_zero():
+    cfg = O.cubic(10, 7.0, order=2, N=4, eta=0.0)
+    R, Z = inputs.atoms(32, 2, 7.0, "const4")
+    vext = O.vext_gaussians(cfg, R, Z, 0.8)
+    st = O.run(inputs.random_orbitals(32, 4, cfg.n), vext, cfg, 80)
+    E = [O.initial_state(inputs.random_orbitals(32, 4, cfg.n), vext, cfg).E] + [h.energy for h in st.history]
+    assert all(b <= a + 1e-12 for a, b in zip(E, E[1:]))
+
+
+def test_bb_steps_cauchy_schwarz_and_scalar_case():
+    cfg = O.cubic(4, 2.0, N=2)
+    rng = np.random.default_rng(4)
+    S = rng.standard_normal((2,) + cfg.shape)
+    Y = rng.standard_normal((2,) + cfg.shape)
+    t1 = O.bb_step(S, Y, O.Config(n=cfg.n, L=cfg.L, bb_variant=1), 0)
+    t2 = O.bb_step(S, Y, O.Config(n=cfg.n, L=cfg.L, bb_variant=2), 0)
+    assert t1 >= t2 > 0
+    # Y = c S (a quadratic with Hessian c I): both steps equal 1/c
+    for v in (1, 2):
+        assert O.bb_step(S, 2.5 * S, O.Config(n=cfg.n, L=cfg.L, bb_variant=v), 0) == pytest.approx(0.4, rel=1e-14)
+
+
+def test_optm_qr_and_opt_par_agree():
+    """Table 1 claim: Opt-Par reaches the same energy as OptM-QR (full Sigma)."""
+    cfg = O.cubic(10, 7.0, order=2, N=4)
+    R, Z = inputs.atoms(41, 2, 7.0, "const4")
+    vext = O.vext_gaussians(cfg, R, Z, 0.8)
+    U0 = inputs.random_orbitals(41, 4, cfg.n)
+    a = O.run(U0, vext, cfg, 3000, e_tol=1e-16)
+    b = O.run(U0, vext, cfg, 3000, e_tol=1e-16, full_sigma=True)
+    assert abs(a.E - b.E) < 1e-8
+
+
+def test_algorithm_m_variants_reach_same_energy():
+    cfg = O.cubic(10, 7.0, order=2, N=4)
+    R, Z = inputs.atoms(41, 2, 7.0, "const4")
+    vext = O.vext_gaussians(cfg, R, Z, 0.8)
+    U0 = inputs.random_orbitals(41, 4, cfg.n)
+    a = O.run(U0, vext, cfg, 3000, e_tol=1e-16)
+    cfgm = O.cubic(10, 7.0, order=2, N=4, n_diag=20)
+    b = O.run(U0, vext, cfgm, 3000, e_tol=1e-16)
+    assert abs(a.E - b.E) < 1e-8
