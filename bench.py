@@ -1,0 +1,420 @@
+"""Benchmark: outer iterations/s of the parallel orbital-updating iteration.
+
+Default workload: periodic L=30 bohr, 160^3 grid, 13-point Laplacian, 64
+Gaussian-well atoms, N=128 orbitals, mixed form (FP32 bulk; FP64 Cholesky,
+density, Hartree FFT and energy/trace reductions), forces from the adjoint
+every 10 steps.  One step = one accepted iteration of Algorithm E (including
+any rejected trials of that step).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME] [--precision fp32|fp64] [--ttt]
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs an independent
+replica on its own GPU (the path has no exchange step); value is the sum of
+all ranks' iterations over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1510_07230_gb300 import inputs  # noqa: E402
+
+METRIC = "outer iterations/s (160^3, N=128, 13-point, mixed form)"
+UNIT = "iterations/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="l30_g160_n128")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--bb-variant", type=int, default=1)
+    ap.add_argument("--force-every", type=int, default=10)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ttt", action="store_true", help="time-to-1e-6 Ha, mixed vs FP64 (long)")
+    ap.add_argument("--ttt-max", type=int, default=4000)
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------- helpers
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes(name, N, ng, s):
+    """Algorithmic DRAM bytes of one launch (halo re-reads count as zero)."""
+    B = N * ng * s
+    table = {
+        "apply_h": 4 * B + ng * s,                # W, W', HW' in, HW out, V
+        "rotate_density": 3 * B + 8 * ng,         # W, HW in, W_new out, rho out
+        "gram": 2 * B,                            # W, HW in (split partials are small)
+        "fft_x_fwd": 8 * ng + 16 * ng,
+        "fft_y_fwd": 32 * ng,
+        "fft_z_poisson": 32 * ng,
+        "fft_y_inv": 32 * ng,
+        "fft_x_inv_potential": 16 * ng + 8 * ng * 2 + 8 * ng + s * ng,
+    }
+    return table.get(name)
+
+
+def gram_flops(N, ng):
+    return N * (N + 1) * ng  # upper triangle, one FMA = 2 flops
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch from a committed ncu summary, if it is current."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        ent = d.get(kernel)
+        if not ent:
+            return None
+        src = os.path.join(ROOT, ent["source"])
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        return ent["bytes_per_launch"] if h == ent["source_sha"] else None
+    except Exception:
+        return None
+
+
+# --------------------------------------------------------------- CPU oracle sample
+ORACLE_SAMPLE_CODE = r"""
+import json, os, sys, time
+sys.path.insert(0, %(root)r)
+import numpy as np
+from oracle import pou_oracle as O
+from paper_1510_07230_gb300 import inputs
+w, R, Z = inputs.WORKLOADS[%(wl)r], None, None
+R, Z = inputs.atoms(w.seed, w.n_atoms, w.L, w.z_recipe)
+Ns = %(ns)d
+U0 = inputs.random_orbitals(w.seed, w.N, (w.n, w.n, w.n), count=Ns)
+cfg = O.cubic(w.n, w.L, order=w.order, N=Ns)
+vext = O.vext_gaussians(cfg, R, Z, w.width)
+st = O.initial_state(U0, vext, cfg)
+times = []
+for k in range(%(steps)d):
+    t = time.perf_counter()
+    O.iterate(st, vext, cfg)
+    times.append(time.perf_counter() - t)
+print(json.dumps({"times": times}))
+"""
+
+
+def run_oracle_sample(workload, ns, steps):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    code = ORACLE_SAMPLE_CODE % {"root": ROOT, "wl": workload, "ns": ns, "steps": steps}
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])["times"]
+
+
+def cpu_baseline(workload, steps=2, ns=8):
+    w = inputs.WORKLOADS[workload]
+    times = run_oracle_sample(workload, ns, steps)
+    per_iter = statistics.mean(times) * (w.N / ns)
+    return {"value": 1.0 / per_iter, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"{steps} oracle iterations on the first {ns} of the {w.N} orbitals of the same "
+                       f"{w.n}^3 workload (FP64 NumPy, 1 BLAS thread), time scaled by {w.N}/{ns}; the "
+                       f"scaling ignores the N^2 Gram/rotation terms, so this overstates the oracle rate"),
+            "seconds_measured": sum(times)}
+
+
+# --------------------------------------------------------------- our arm
+def make_solver(pou, w, precision, stream_ptr, bb_variant):
+    s = pou.Solver(w.n, w.L, w.N, order=w.order, precision=precision, stream=stream_ptr,
+                   bb_variant=bb_variant)
+    return s
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1510_07230_gb300 import pou
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    w = inputs.WORKLOADS[args.workload]
+    R, Z = inputs.atoms(w.seed, w.n_atoms, w.L, w.z_recipe)
+    t0 = time.time()
+    U0 = inputs.random_orbitals(w.seed, w.N, (w.n, w.n, w.n))
+    gen_s = time.time() - t0
+    prec = pou.FP32 if args.precision == "fp32" else pou.FP64
+    stream = torch.cuda.Stream()
+    s = make_solver(pou, w, prec, stream.cuda_stream, args.bb_variant)
+    s.set_atoms(R, Z, w.width)
+    s.set_orbitals(U0)
+    K, W = args.steps, args.warmup
+    fe = args.force_every
+
+    def step(i):
+        s.iterate(1)
+        if fe > 0 and (i + 1) % fe == 0:
+            s.backward(None, 1.0, None, atoms=True)
+
+    for i in range(W):
+        step(i)
+    s.set_profiling(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clock = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = s.launch_count()
+    passes = 0
+    ev0.record(stream)
+    for i in range(K):
+        rep = s.iterate(1)
+        passes += rep["passes"]
+        if fe > 0 and (i + 1) % fe == 0:
+            s.backward(None, 1.0, None, atoms=True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clock.stop()
+    ms = ev0.elapsed_time(ev1)
+    launches = s.launch_count() - launches0
+    prof = s.profile()
+    s.set_profiling(False)
+    E_final = s.energy()["total"]
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * K / (ms / 1e3)
+
+    # roofline of the dominant kernel (live CUDA-event times on the library's stream)
+    esz = 4 if prec == pou.FP32 else 8
+    ng = w.n ** 3
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (nl, tms) = dom
+    per_launch_s = tms / nl / 1e3
+    peaks, src = measured_peaks()
+    if name == "gram" and prec == pou.FP32:
+        fl = gram_flops(w.N, ng)
+        fp32_peak = 152 * 128 * 2 * (peaks.get("sm_max_mhz", 2070.0) * 1e6) / 1e12
+        roof = {"bound": "alu", "kernel": name, "achieved": fl / per_launch_s / 1e12, "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": fl / per_launch_s / 1e12 / fp32_peak, "traffic": traffic_for(name),
+                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flops x max SM clock"}
+    else:
+        b = algorithmic_bytes(name, w.N, ng, esz)
+        ach = b / per_launch_s / 1e9 if b else None
+        roof = {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": (ach / peaks["hbm_gbs"]) if ach else None, "traffic": traffic_for(name),
+                "peak_source": f"hbm_gbs of {src}"}
+    kernels = {}
+    for k, (n_, t_) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
+        b = algorithmic_bytes(k, w.N, ng, esz)
+        kernels[k] = {"launches": n_, "ms_total": round(t_, 3), "share": round(t_ / sum(v[1] for v in prof.values()), 4),
+                      "gbs": round(b / (t_ / n_ / 1e3) / 1e9, 1) if b else None}
+    iter_kernels = [k for k in prof if k not in ("density", "forces", "potential_local", "convert", "scale_copy")]
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == pou.FP32 else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "grid": f"{w.n}^3", "L_bohr": w.L, "stencil_points": 7 if w.order == 2 else 13,
+                   "atoms": w.n_atoms, "N": w.N, "precision": "mixed: FP32 bulk, FP64 Cholesky/FFT/energies"
+                   if prec == pou.FP32 else "FP64", "bb_variant": args.bb_variant, "forces_every": fe,
+                   "l2": "inputs larger than L2 (orbital block %.2f GB)" % (w.N * ng * esz / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "passes": passes, "gpu_launches": launches, "roofline": roof, "kernels": kernels,
+        "energy_final": E_final, "clocks": clocks, "input_generation_s": round(gen_s, 1),
+    }
+    out["_iter_kernels"] = iter_kernels
+
+    # FP64 form beside it (same workload, same U0)
+    if prec == pou.FP32 and args.fp64_steps > 0:
+        s64 = make_solver(pou, w, pou.FP64, stream.cuda_stream, args.bb_variant)
+        s64.set_atoms(R, Z, w.width)
+        s64.set_orbitals(U0)
+        s64.iterate(1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s64.iterate(args.fp64_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1)
+        out["fp64_form"] = {"value": args.fp64_steps / (t64 / 1e3), "unit": UNIT, "steps": args.fp64_steps,
+                            "ms_per_step": t64 / args.fp64_steps}
+        s64.close()
+
+    # end to end through the public API with host buffers
+    if not args.no_e2e:
+        Kh = max(5, min(K, 20))
+        host = torch.empty(U0.shape, dtype=torch.float32 if prec == pou.FP32 else torch.float64, pin_memory=True)
+        host.copy_(torch.from_numpy(U0))
+        outh = torch.empty_like(host, pin_memory=True)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        s.set_orbitals(host)
+        for i in range(Kh):
+            s.iterate(1)          # reads the step's energy back to the host
+        s.get_orbitals(outh)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t
+        blk = host.numel() * host.element_size()
+        out["e2e"] = {"value": world * Kh / te, "unit": UNIT, "steps": Kh,
+                      "h2d_bytes_per_step": blk / Kh, "d2h_bytes_per_step": blk / Kh + 512,
+                      "includes": "set_orbitals (pinned host block, Cholesky-QR, potential, energy) + "
+                                  "steps + get_orbitals to pinned host"}
+    s.close()
+
+    if args.ttt:
+        out["time_to_1e-6"] = time_to_tolerance(pou, torch, w, R, Z, U0, stream, args)
+
+    if rank == 0:
+        if not args.no_cpu:
+            try:
+                out["cpu_baseline"] = cpu_baseline(args.workload)
+            except Exception as e:  # keep the GPU line even if the host run fails
+                out["cpu_baseline"] = {"value": None, "error": str(e)[-300:]}
+        out.pop("_iter_kernels", None)
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def time_to_tolerance(pou, torch, w, R, Z, U0, stream, args):
+    """Wall time until |E_l - E*| <= 1e-6 Ha for the FP64 and mixed forms."""
+    res = {}
+    curves = {}
+    for prec, label in ((pou.FP64, "fp64"), (pou.FP32, "mixed")):
+        s = make_solver(pou, w, prec, stream.cuda_stream, args.bb_variant)
+        s.set_atoms(R, Z, w.width)
+        s.set_orbitals(U0)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        times, done = [], 0
+        while done < args.ttt_max:
+            s.iterate(50)
+            done += 50
+            times.append((done, time.perf_counter() - t))
+        E, _ = s.history()
+        curves[label] = (E, times)
+        s.close()
+    E64 = curves["fp64"][0]
+    Estar = float(np.min(E64))
+    for label, (E, times) in curves.items():
+        hit = np.nonzero(np.abs(E - Estar) <= 1e-6)[0]
+        if len(hit) == 0:
+            res[label] = {"reached": False, "iterations": len(E), "final_error": float(E[-1] - Estar)}
+            continue
+        it = int(hit[0]) + 1
+        # wall time at that iteration, interpolated within the 50-step chunk
+        for d, tt in times:
+            if d >= it:
+                prev = [x for x in times if x[0] < d]
+                t0, d0 = (prev[-1][1], prev[-1][0]) if prev else (0.0, 0)
+                sec = t0 + (tt - t0) * (it - d0) / (d - d0)
+                break
+        res[label] = {"reached": True, "iterations": it, "seconds": sec}
+    res["E_star"] = Estar
+    res["E_star_definition"] = f"lowest FP64-form energy within {args.ttt_max} steps"
+    return res
+
+
+# --------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = inputs.WORKLOADS[args.workload]
+    ns = 8
+    total = args.warmup + args.steps
+    times = run_oracle_sample(args.workload, ns, total)
+    timed = times[args.warmup:]
+    per_iter = statistics.mean(timed) * (w.N / ns)
+    value = 1.0 / per_iter
+    sample = (f"each step: one oracle iteration on the first {ns} of the {w.N} orbitals of the "
+              f"{w.n}^3 workload (FP64 NumPy, 1 BLAS thread), time scaled by {w.N}/{ns}")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_iter * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": args.workload, "grid": f"{w.n}^3", "N": w.N},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -142,7 +142,26 @@ def vext_gaussians(cfg: Config, R: np.ndarray, Z: np.ndarray, width: float) -> n
     Stands in for the local pseudopotential of Sec. 2.1; the sum runs over the
     27 nearest periodic images n in {-1, 0, 1}^3 of the position wrapped into
     [0, L) (so every grid point sees its nearest image of every atom).
+    Because exp(-|d|^2/(2 w^2)) is a product over the three axes, the 27-term
+    image sum equals the product of the three per-axis sums over n_a in
+    {-1, 0, 1} (distributivity); it is evaluated in that form.  The literal
+    27-term sum is ``vext_gaussians_literal``.
     """
+    x, y, z = grid_coords(cfg)
+    Lx, Ly, Lz = (float(v) for v in cfg.L)
+    R = wrap_positions(R, cfg)
+    V = np.zeros(cfg.shape)
+    two_s2 = 2.0 * width * width
+    for I in range(len(Z)):
+        gx = sum(np.exp(-(x - R[I, 0] - a * Lx) ** 2 / two_s2) for a in (-1, 0, 1))
+        gy = sum(np.exp(-(y - R[I, 1] - b * Ly) ** 2 / two_s2) for b in (-1, 0, 1))
+        gz = sum(np.exp(-(z - R[I, 2] - c * Lz) ** 2 / two_s2) for c in (-1, 0, 1))
+        V -= Z[I] * gz[:, None, None] * gy[None, :, None] * gx[None, None, :]
+    return V
+
+
+def vext_gaussians_literal(cfg: Config, R: np.ndarray, Z: np.ndarray, width: float) -> np.ndarray:
+    """The same wells as ``vext_gaussians``, summed image by image (27 terms per atom)."""
     x, y, z = grid_coords(cfg)
     Lx, Ly, Lz = (float(v) for v in cfg.L)
     R = wrap_positions(R, cfg)

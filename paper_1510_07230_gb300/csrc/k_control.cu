@@ -1,0 +1,174 @@
+// Controller of one pass of Algorithm E (Sec. 3.2), one CTA:
+//   * reduces the H-apply sums of the trial block and the potential-pass
+//     energy sums (fixed order, deterministic),
+//   * E(W(tau)) = kinetic + external + Hartree + exchange (Eq. energy),
+//   * nonmonotone test E(W(tau)) <= C^l - rho1 tau ||Z^l||_F^2 (Eq. ene-de);
+//     on failure tau <- tau delta (the next pass rebuilds the trial from the
+//     kept W^l, HW^l); after max_backtrack reductions the trial is accepted
+//     and counted,
+//   * on acceptance: Q^(l+1) = eta Q^l + 1, C^(l+1) = (eta Q^l C^l + E)/Q^(l+1),
+//     the pair holding W^(l+1) becomes current, sigma_ii = <H w_i, w_i>,
+//     ||Z||_F^2 and the Barzilai-Borwein step for the next step from
+//     S = W^(l+1) - W^l and Y = Z^(l+1) - Z^l, using
+//       tr<S^T S> = dV sum p_ss,
+//       tr<S^T Y> = dV sum (p_sb - dsigma p_sw),
+//       tr<Y^T Y> = dV sum (p_bb - 2 dsigma p_bw + dsigma^2 p_ww),
+//     with dsigma_i = sigma_i - sigma'_i (Y = b - dsigma w).
+#include "pou_internal.cuh"
+
+namespace pou {
+
+namespace {
+
+constexpr int KNT = 256;
+
+__device__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double r = 0.0;
+  for (int w = 0; w < KNT / 32; ++w) r += sh[w];
+  return r;
+}
+
+__global__ void __launch_bounds__(KNT) k_control(CtrlArgs a) {
+  __shared__ double sh[KNT / 32];
+  __shared__ double esum[NE];
+  State* st = a.st;
+  if (st->done) return;
+  const int cur = st->cur;
+  const int t = 1 - cur;
+  const int N = a.N;
+  const int tid = threadIdx.x;
+  double* part = a.part[t];
+  // per-orbital sums over tiles (fixed order)
+  for (int idx = tid; idx < N * NP; idx += KNT) {
+    const int i = idx / NP, k = idx % NP;
+    const double* src = a.tilepart + (i64)i * a.ntile * NP + k;
+    double s = 0.0;
+    for (int j = 0; j < a.ntile; ++j) s += src[(i64)j * NP];
+    part[idx] = s;
+  }
+  if (tid < NE) {
+    double s = 0.0;
+    for (int b = 0; b < a.neblk; ++b) s += a.epart[(i64)b * NE + tid];
+    esum[tid] = s;
+  }
+  __syncthreads();
+  const double dV = a.dV;
+  double kin = 0.0, ss = 0.0, sy = 0.0, yy = 0.0, zz = 0.0;
+  for (int i = tid; i < N; i += KNT) {
+    const double* p = part + i * NP;
+    const double sig = dV * p[P_HW];
+    a.sigma[t][i] = sig;
+    kin += p[P_KIN];
+    zz += p[P_HH] - 2.0 * sig * p[P_HW] + sig * sig * p[P_WW];
+    if (!a.init) {
+      const double ds = sig - a.sigma[cur][i];
+      ss += p[P_SS];
+      sy += p[P_SB] - ds * p[P_SW];
+      yy += p[P_BB] - 2.0 * ds * p[P_BW] + ds * ds * p[P_WW];
+    }
+  }
+  kin = block_sum(kin, sh);
+  zz = block_sum(zz, sh);
+  ss = block_sum(ss, sh);
+  sy = block_sum(sy, sh);
+  yy = block_sum(yy, sh);
+  if (tid != 0) return;
+
+  const double ekin = F_OCC * dV * kin;
+  const double eext = dV * esum[E_EXT];
+  const double eh = 0.5 * dV * esum[E_H];
+  const double ex = dV * esum[E_X];
+  const double E = ekin + eext + eh + ex;
+  st->terms_trial[0] = ekin;
+  st->terms_trial[1] = eext;
+  st->terms_trial[2] = eh;
+  st->terms_trial[3] = ex;
+  zz *= dV;
+  ss *= dV;
+  sy = fabs(sy * dV);
+  yy *= dV;
+  if (!isfinite(E)) {
+    st->status = 5;  // POU_ENAN
+    st->done = 1;
+    return;
+  }
+  if (a.init) {
+    st->cur = t;
+    st->E_cur = E;
+    for (int k = 0; k < 4; ++k) st->terms_cur[k] = st->terms_trial[k];
+    st->C = E;
+    st->Q = 1.0;
+    st->znorm2 = zz;
+    st->tau_bb = a.tau0;
+    st->tau_trial = a.tau0;
+    st->last_tau = 0.0;
+    st->s = 0;
+    st->l = 0;
+    st->passes = st->backtracks = st->forced = st->n_df = 0;
+    st->df[0] = st->df[1] = st->df[2] = 0.0;
+    st->gram_off_acc = 0.0;
+    st->converged = 0;
+    st->done = 1;
+    return;
+  }
+  st->passes += 1;
+  bool accept = E <= st->C - a.rho1 * st->tau_trial * st->znorm2;
+  if (!accept && st->s >= a.max_backtrack) {
+    accept = true;
+    st->forced += 1;
+  }
+  if (!accept) {
+    st->s += 1;
+    st->backtracks += 1;
+    st->tau_trial = st->tau_bb * pow(a.delta, (double)st->s);
+    return;
+  }
+  const double Qn = a.eta * st->Q + 1.0;
+  st->C = (a.eta * st->Q * st->C + E) / Qn;
+  st->Q = Qn;
+  const double df = fabs(st->E_cur - E) / (fabs(st->E_cur) + 1.0);
+  st->df[2] = st->df[1];
+  st->df[1] = st->df[0];
+  st->df[0] = df;
+  st->n_df += 1;
+  st->last_tau = st->tau_trial;
+  if (st->l < HIST_MAX) {
+    a.hist_E[st->l] = E;
+    a.hist_tau[st->l] = st->tau_trial;
+  }
+  st->E_cur = E;
+  for (int k = 0; k < 4; ++k) st->terms_cur[k] = st->terms_trial[k];
+  st->gram_off_acc = st->gram_off_trial;
+  st->cur = t;
+  st->l += 1;
+  st->znorm2 = zz;
+  // Barzilai-Borwein step shared by all orbitals
+  int variant = a.bb_variant;
+  if (variant == 3) variant = (st->l % 2 == 0) ? 1 : 2;
+  double tau = (variant == 1) ? (sy > 0.0 ? ss / sy : NAN) : (yy > 0.0 ? sy / yy : NAN);
+  if (!isfinite(tau) || tau <= 0.0) tau = a.tau0;
+  tau = fmin(fmax(tau, a.tau_min), a.tau_max);
+  st->tau_bb = tau;
+  st->tau_trial = tau;
+  st->s = 0;
+  if (st->l >= st->target_l) st->done = 1;
+  if (st->e_tol > 0.0 && st->n_df >= 3 && (st->df[0] + st->df[1] + st->df[2]) / 3.0 < st->e_tol) {
+    st->converged = 1;
+    st->done = 1;
+  }
+}
+
+}  // namespace
+
+void launch_control(const CtrlArgs& a, cudaStream_t s) {
+  prof_begin("control", s);
+  k_control<<<1, KNT, 0, s>>>(a);
+  prof_end(s);
+}
+
+}  // namespace pou

@@ -1,0 +1,225 @@
+// Internal declarations shared by the translation units of libpou.so.
+// Not part of the public C-ABI (see include/pou.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+namespace pou {
+
+typedef long long i64;
+
+// Per-orbital raw sums (no dV factor) produced by the H-apply pass for the
+// block W it reads, against the current iterate W' (prev) and its HW'.
+//   s = w - w',  b = (hw - hw') - sigma' s  (so that Y = Z - Z' = b - (sigma - sigma') w)
+enum { P_WW = 0, P_HW, P_HH, P_KIN, P_SS, P_SB, P_SW, P_BB, P_BW, NP };
+// Energy sums of the potential pass: sum rho*Vext, sum rho*V_H, sum eps_x(rho)*rho
+enum { E_EXT = 0, E_H, E_X, NE };
+
+constexpr int HIST_MAX = 16384;
+constexpr double F_OCC = 2.0;
+
+// Iteration state, resident in device memory and updated only by the
+// controller kernel, so that a whole iteration (including the backtracking
+// decision and the buffer swap) runs without a host round trip.
+struct State {
+  double tau_bb;     // Barzilai-Borwein step of the current step l
+  double tau_trial;  // step of the pending trial, tau_bb * delta^s
+  double C, Q;       // nonmonotone reference value and weight (Eq. ene-de)
+  double E_cur;      // E(W^l)
+  double znorm2;     // ||Z^l||_F^2
+  double last_tau;   // step of the last accepted trial
+  double terms_cur[4];
+  double terms_trial[4];
+  double df[3];      // relative energy changes, newest first (Sec. 4.2)
+  double gram_off_trial, gram_off_acc;
+  double e_tol;
+  int cur;           // pair (0/1) holding W^l, HW^l, V^l, rho^l
+  int l;             // accepted steps since the orbitals were set
+  int s;             // step reductions so far in step l
+  int target_l;      // stop once l reaches this
+  int done;          // 1: every kernel of the pass returns at once
+  int status;        // 0, or a pou_status breakdown code
+  int converged;
+  int passes, backtracks, forced, n_df;
+  int chol_info;
+};
+
+// ---------------------------------------------------------------- stencil
+template <typename T>
+struct ApplyArgs {
+  const State* st;      // nullptr: explicit mode
+  const T* W[2];
+  T* HW[2];
+  const T* V[2];
+  const double* sigma[2];
+  int mode;             // 0: trial vs current, 1: trial without history, 2: explicit W[0],V[0]->HW[0]
+  double* tilepart;     // [N][ntile][NP] or nullptr
+  T out_scale;
+  int N, nx, ny, nz, nzc;
+  T ihx2, ihy2, ihz2;
+};
+template <typename T>
+void launch_apply_h(const ApplyArgs<T>& a, int order, cudaStream_t s, int* ntile_out);
+int apply_h_ntile(int nx, int ny, int nz, int N, int* nzc_out);
+
+// ---------------------------------------------------------------- gram / rotation
+template <typename T>
+struct GramArgs {
+  const State* st;      // iteration mode (trial == 1): source W[cur], HW[cur], sigma[cur], tau_trial
+  const T* W[2];
+  const T* HW[2];
+  const double* sigma[2];
+  const T* A;           // plain mode: A (and B for the general product)
+  const T* B;           // general product A^T B (all blocks) when non-null
+  int trial;
+  i64 ng;
+  int N;
+  double* split;        // [nsplit][npair][ST*ST]
+};
+template <typename T>
+int gram_supertile();
+template <typename T>
+void gram_layout(i64 ng, int N, bool general, int* nsplit, int* npair, i64* chunk);
+template <typename T>
+void launch_gram(const GramArgs<T>& a, cudaStream_t s);
+
+struct GramReduceArgs {
+  const State* st;
+  const double* split;
+  int nsplit, npair, ST, N;
+  int general;          // 1: all blocks computed (A^T B); 0: upper super-tiles, symmetric
+  double dV;
+  double* S;            // N*N
+  // diagonal replacement for the trial Gram (iteration mode)
+  int trial;
+  const double* sigma[2];
+  const double* part[2];
+  int fp32_coef;        // coefficients rounded to FP32 as in the FP32 kernels
+};
+void launch_gram_reduce(const GramReduceArgs& a, cudaStream_t s);
+
+template <typename T>
+struct RotArgs {
+  const State* st;      // iteration mode: A = W~ from W[cur], HW[cur]; out W[1-cur], rho[1-cur]
+  const T* W[2];
+  const T* HW[2];
+  const double* sigma[2];
+  T* Wout[2];
+  double* rho[2];
+  const T* A;           // explicit mode source
+  T* B;                 // explicit mode destination
+  double* rho_out;      // explicit mode density (nullable)
+  const double* Rinv;   // N*N FP64 (upper)
+  int trial;
+  i64 ng;
+  int N;
+  int general;          // 1: full matrix (no triangular skip)
+};
+template <typename T>
+void launch_rotate(const RotArgs<T>& a, cudaStream_t s);
+
+template <typename T>
+void launch_density(const T* U, i64 ng, int N, double* rho, cudaStream_t s);
+void launch_convert_f64_f32(const double* in, float* out, i64 n, cudaStream_t s);
+void launch_convert_f32_f64(const float* in, double* out, i64 n, cudaStream_t s);
+template <typename T>
+void launch_scale_copy(const T* in, T* out, T scale, i64 n, cudaStream_t s);
+
+// ---------------------------------------------------------------- cholesky
+void launch_cholinv(const State* st, const double* S, double* Rinv, int N, int* info,
+                    State* st_rw, double piv_rel, cudaStream_t s);
+size_t cholinv_smem_bytes(int N);
+
+// ---------------------------------------------------------------- fft / potential
+struct FftPlan {
+  int n[3];
+  int nst[3];
+  int radix[3][8];
+  double2* tw[3];       // device, n[a] entries exp(-2 pi i k / n)
+  double* g2[3];        // device, (2 pi m / L)^2, m in FFT order
+  int lb[3];            // lines per block
+  double* mem;          // one allocation holding all tables
+};
+bool fft_supported(int n);
+int fft_plan_create(FftPlan* p, const int n[3], const double L[3]);
+void fft_plan_destroy(FftPlan* p);
+
+template <typename T>
+struct PotArgs {
+  const State* st;      // iteration mode: rho[1-cur] -> V[1-cur]
+  const double* rho[2];
+  double* V64[2];
+  T* V[2];
+  const double* rho_x;  // explicit mode
+  double* V64_x;
+  T* V_x;
+  double* vh_out;       // stand-alone Hartree: write V_H only
+  const double* vext;
+  double2* work;
+  double* epart;        // [nblk][NE]
+  int hartree, exchange;
+};
+template <typename T>
+int launch_potential(const FftPlan& p, const PotArgs<T>& a, cudaStream_t s);  // returns nblk
+
+// ---------------------------------------------------------------- atoms
+struct AtomTables {
+  double* gx; double* gy; double* gz;      // [M][n]
+  double* dgx; double* dgy; double* dgz;   // [M][n]
+  int* win;                                // [M][3][2] window start, length
+};
+void launch_atom_tables(const double* R, const double* Z, int M, double width, const int n[3],
+                        const double L[3], const AtomTables& t, cudaStream_t s);
+void launch_vext(const double* Z, int M, const int n[3], const AtomTables& t, double* vext,
+                 cudaStream_t s);
+int launch_forces(const double* rho, const double* Z, int M, const int n[3], const AtomTables& t,
+                  double* fpart, cudaStream_t s);  // returns z splits; fpart [M][split][4]
+
+// ---------------------------------------------------------------- controller
+struct CtrlArgs {
+  State* st;
+  double* hist_E;
+  double* hist_tau;
+  double* sigma[2];
+  double* part[2];
+  const double* tilepart;
+  int ntile;
+  const double* epart;
+  int neblk;
+  int N;
+  int init;
+  double dV, rho1, delta, eta, tau0, tau_min, tau_max;
+  int bb_variant, max_backtrack;
+};
+void launch_control(const CtrlArgs& a, cudaStream_t s);
+
+// Shared-memory opt-ins of the kernels that need more than 48 KB; called
+// once per process before any launch (and before any graph capture).
+void configure_rotate();
+void configure_cholinv();
+void configure_fft();
+void configure_kernels();
+
+// Counts every kernel launched by the library (host side).
+extern long long g_launches;
+
+// Per-kernel CUDA-event timing.  When a context enables profiling it installs
+// a recorder for the calling thread; every launch site brackets its kernel
+// with prof_begin / prof_end, which record events on the launch stream.
+struct ProfRecorder {
+  virtual void begin(const char* name, cudaStream_t s) = 0;
+  virtual void end(cudaStream_t s) = 0;
+  virtual ~ProfRecorder() {}
+};
+extern thread_local ProfRecorder* g_prof;
+inline void prof_begin(const char* name, cudaStream_t s) {
+  if (g_prof) g_prof->begin(name, s);
+}
+inline void prof_end(cudaStream_t s) {
+  ++g_launches;
+  if (g_prof) g_prof->end(s);
+}
+
+}  // namespace pou

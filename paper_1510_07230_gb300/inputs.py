@@ -90,14 +90,17 @@ def atoms(seed: int, n_atoms: int, L: float, z_recipe: str,
     return R, Z
 
 
-def random_orbitals(seed: int, N: int, n: Tuple[int, int, int]) -> np.ndarray:
+def random_orbitals(seed: int, N: int, n: Tuple[int, int, int], count: Optional[int] = None) -> np.ndarray:
     """Raw initial orbitals, i.i.d. N(0,1), shape (N, nz, ny, nx), float64.
 
     They are not orthonormal: each solver orthonormalises them itself.
+    ``count`` < N returns only the first ``count`` orbitals of the same draw
+    (the generator fills the array in order, so they are identical).
     """
     nx, ny, nz = n
     rng = np.random.Generator(np.random.PCG64(seed + 1000003))
-    return rng.standard_normal((N, nz, ny, nx))
+    k = N if count is None else min(int(count), N)
+    return rng.standard_normal((k, nz, ny, nx))
 
 
 def random_field(seed: int, n: Tuple[int, int, int], lo: float = 0.0,

@@ -1,0 +1,79 @@
+"""The C-ABI library loads without a GPU and exports what include/pou.h declares."""
+import ctypes as C
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+LIB = os.path.join(ROOT, "paper_1510_07230_gb300", "libpou.so")
+
+
+@pytest.fixture(scope="module")
+def pou():
+    if not os.path.exists(LIB):
+        from paper_1510_07230_gb300 import build
+        build.build()
+    from paper_1510_07230_gb300 import pou as P
+    return P
+
+
+def test_every_declared_function_is_exported(pou):
+    names = pou.header_functions()
+    assert len(names) >= 25
+    missing = [n for n, ok in pou.library_exports(names).items() if not ok]
+    assert not missing, missing
+
+
+def test_exported_symbols_with_nm(pou):
+    out = subprocess.run(["nm", "-D", "--defined-only", LIB], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    for n in pou.header_functions():
+        assert n in exported, n
+
+
+def test_config_default_is_the_papers_constants(pou):
+    cfg = pou.Config()
+    pou._lib.pou_config_default(C.byref(cfg))
+    assert cfg.rho1 == 1e-4 and cfg.delta == 0.1 and cfg.eta == 0.85
+    assert cfg.n_org == 1 and cfg.n_diag == 0 and cfg.bb_variant == 1
+    assert cfg.max_backtrack == 10 and cfg.stencil_order == 2
+
+
+@pytest.mark.parametrize("field,value", [
+    ("N", 0), ("N", 129), ("stencil_order", 3), ("precision", 7), ("bb_variant", 0),
+    ("delta", 1.5), ("eta", -0.1), ("n_org", 2), ("n_diag", 100), ("tau_min", 0.0),
+])
+def test_invalid_configs_rejected_before_touching_the_device(pou, field, value):
+    cfg = pou.make_config(16, 8.0, 4)
+    setattr(cfg, field, value)
+    ctx = C.c_void_p()
+    assert pou._lib.pou_create(C.byref(cfg), C.byref(ctx)) == pou.EINVAL
+    assert not ctx.value
+
+
+def test_invalid_grid_rejected(pou):
+    for n in [(7, 8, 8), (16, 1, 16), (0, 8, 8)]:  # 7 is not 2^a 3^b 5^c
+        cfg = pou.make_config(n, 8.0, 2)
+        ctx = C.c_void_p()
+        assert pou._lib.pou_create(C.byref(cfg), C.byref(ctx)) == pou.EINVAL
+
+
+def test_null_arguments(pou):
+    assert pou._lib.pou_create(None, None) == pou.EINVAL
+    assert pou._lib.pou_iterate(None, 1, 0.0, 0.0, None) == pou.EINVAL
+    pou._lib.pou_destroy(None)
+    assert pou._lib.pou_launch_count(None) == 0
+
+
+def test_workspace_sizes(pou):
+    assert pou.gram_workspace_bytes(pou.DT_F64, 4096, 100) > 0
+    assert pou.hartree_workspace_bytes((8, 6, 10)) == 8 * 6 * 10 * 16
+
+
+def test_product_path_does_not_import_the_oracle():
+    code = ("import sys; import paper_1510_07230_gb300.pou, paper_1510_07230_gb300.autograd; "
+            "print(any(m == 'oracle' or m.startswith('oracle.') for m in sys.modules))")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT)
+    assert r.stdout.strip() == "False", r.stderr

@@ -1,0 +1,441 @@
+"""GPU-vs-oracle parity for every step of the hot path, through the C-ABI.
+
+Tolerances.  FP64 form: the kernels reorder FP64 sums, so results agree to a
+few ulps times the condition of each quantity; energies to 1e-8 Ha over a
+200-step trajectory (the benchmark spec's bound).  FP32 form: inputs are rounded to
+FP32 first and the oracle runs on the rounded values, so the remaining error
+is FP32 arithmetic (2^-24 relative per operation, random sign, summed in FP64
+at the block level): 1e-5 relative for pointwise fields, 1e-6 Ha for energies.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import pou_oracle as O
+from paper_1510_07230_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def P():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1510_07230_gb300 import pou
+    return pou
+
+
+def dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def ocfg(n, L, N, order=2, hartree=1, exchange=1, **kw):
+    n = (n, n, n) if np.isscalar(n) else tuple(n)
+    L = (L, L, L) if np.isscalar(L) else tuple(L)
+    return O.Config(n=n, L=L, order=order, N=N, hartree=hartree, exchange=exchange, **kw)
+
+
+def solver(P, n, L, N, order=2, precision=0, **kw):
+    return P.Solver(n, L, N, order=order, precision=precision, **kw)
+
+
+# ------------------------------------------------------------------ a3: Gram
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+@pytest.mark.parametrize("N,ng", [(1, 37), (5, 2160), (64, 20000), (100, 50000), (128, 4099)])
+def test_gram_op(P, dt, N, ng):
+    rng = np.random.default_rng(N * 7 + ng)
+    A = rng.standard_normal((N, ng))
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    Ad = dev(A, tdt)
+    code = P.DT_F64 if dt == "f64" else P.DT_F32
+    ws = torch.empty(P.gram_workspace_bytes(code, ng, N) // 8 + 1, dtype=torch.float64, device="cuda")
+    S = torch.empty((N, N), dtype=torch.float64, device="cuda")
+    dV = 0.37
+    P.gram(Ad, dV, S, ws)
+    Ar = Ad.double().cpu().numpy()
+    ref = dV * Ar @ Ar.T
+    scale = dV * np.sqrt(np.outer(np.sum(Ar * Ar, 1), np.sum(Ar * Ar, 1)))
+    err = np.max(np.abs(S.cpu().numpy() - ref) / scale)
+    assert err < (1e-13 if dt == "f64" else 2e-6), err
+
+
+# ------------------------------------------------------------------ a4: Cholesky / inverse
+@pytest.mark.parametrize("N", [1, 7, 64, 100, 128])
+def test_cholinv_op(P, N):
+    rng = np.random.default_rng(N)
+    B = rng.standard_normal((N, N)) * 0.1
+    S = np.eye(N) + B @ B.T
+    Sd = dev(S)
+    Rinv = torch.empty_like(Sd)
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    P.cholinv(Sd, Rinv, info)
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    import scipy.linalg as sl
+    R = sl.cholesky(S, lower=False)
+    np.testing.assert_allclose(Rinv.cpu().numpy(), np.linalg.inv(R), atol=1e-12 * np.linalg.cond(R))
+    np.testing.assert_allclose(np.tril(Rinv.cpu().numpy(), -1), 0.0)
+
+
+def test_cholinv_reports_non_spd(P):
+    N = 6
+    S = np.eye(N)
+    S[3, 3] = -1.0
+    Rinv = torch.empty((N, N), dtype=torch.float64, device="cuda")
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    P.cholinv(dev(S), Rinv, info)
+    torch.cuda.synchronize()
+    assert int(info.item()) == 4
+
+
+# ------------------------------------------------------------------ a5: rotation + density
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+@pytest.mark.parametrize("N,ng", [(1, 100), (5, 2160), (64, 6000), (128, 4099)])
+def test_rotate_op(P, dt, N, ng):
+    rng = np.random.default_rng(N + ng)
+    A = rng.standard_normal((N, ng))
+    Bm = rng.standard_normal((N, N)) * 0.05
+    R = np.linalg.cholesky(np.eye(N) + Bm @ Bm.T).T
+    Rinv = np.linalg.inv(R)
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    Ad = dev(A, tdt)
+    Bd = torch.empty_like(Ad)
+    rho = torch.empty(ng, dtype=torch.float64, device="cuda")
+    P.rotate(Ad, dev(Rinv), Bd, rho)
+    Ar = Ad.double().cpu().numpy()
+    ref = Rinv.T @ Ar  # rows of A Rinv (columns)
+    tol = 1e-12 if dt == "f64" else 3e-6
+    np.testing.assert_allclose(Bd.double().cpu().numpy(), ref, atol=tol * np.max(np.abs(ref)))
+    np.testing.assert_allclose(rho.cpu().numpy(), 2.0 * np.sum(ref * ref, 0), rtol=tol * 10, atol=tol)
+
+
+# ------------------------------------------------------------------ a6: Hartree
+@pytest.mark.parametrize("n,L", [((20, 12, 15), (7.0, 5.0, 6.0)), ((32, 32, 32), (10.0,) * 3),
+                                 ((16, 10, 9), (4.0, 3.0, 3.3)), ((96, 6, 5), (20.0, 2.0, 2.0))])
+def test_hartree_op(P, n, L):
+    cfg = ocfg(n, L, 1)
+    rho = inputs.random_field(sum(n), n, 0.0, 1.0)
+    ref = O.hartree_potential(rho, cfg)
+    rd = dev(rho)
+    vh = torch.empty_like(rd)
+    ws = torch.empty(P.hartree_workspace_bytes(n) // 8, dtype=torch.float64, device="cuda")
+    P.hartree(n, L, rd, vh, ws)
+    np.testing.assert_allclose(vh.cpu().numpy(), ref, atol=1e-12 * np.max(np.abs(ref)))
+
+
+# ------------------------------------------------------------------ a1, a7: evaluation
+def _system(n, L, N, seed, M=2):
+    cfg = ocfg(n, L, N)
+    Lv = cfg.L
+    R = np.array([[0.3 * Lv[0], 0.4 * Lv[1], 0.6 * Lv[2]], [0.75 * Lv[0], 0.2 * Lv[1], 0.1 * Lv[2]],
+                  [0.5 * Lv[0], 0.9 * Lv[1], 0.45 * Lv[2]]])[:M]
+    Z = np.array([3.0, 2.0, 4.0])[:M]
+    U = inputs.random_orbitals(seed, N, cfg.n)
+    return R, Z, U
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("order", [2, 4])
+def test_evaluate_energy_terms(P, precision, order):
+    n, L, N = (20, 12, 10), (7.0, 5.0, 4.5), 3
+    R, Z, U = _system(n, L, N, 5)
+    if precision == 1:
+        U = U.astype(np.float32).astype(np.float64)
+    cfg = ocfg(n, L, N, order=order)
+    s = solver(P, n, L, N, order=order, precision=precision)
+    s.set_atoms(R, Z, 0.8)
+    got = s.evaluate(U)
+    ref = O.energy_terms(U, O.vext_gaussians(cfg, R, Z, 0.8), cfg)
+    tol = 1e-11 if precision == 0 else 2e-6
+    for k in ("kinetic", "external", "hartree", "exchange"):
+        assert abs(got[k] - getattr(ref, k)) <= tol * max(1.0, abs(getattr(ref, k))), k
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("order,n", [(2, (20, 12, 10)), (4, (20, 12, 10)), (4, (5, 6, 8)), (2, (27, 9, 4))])
+def test_apply_h_through_adjoint(P, precision, order, n):
+    """a1: HW = -1/2 Lap_h W + V W, read through dE/dU = 2 f dV H U with g = 1/(2 f dV)."""
+    L, N = (6.0, 5.0, 4.0), 2
+    R, Z, U = _system(n, L, N, 9)
+    if precision == 1:
+        U = U.astype(np.float32).astype(np.float64)
+    cfg = ocfg(n, L, N, order=order)
+    s = solver(P, n, L, N, order=order, precision=precision)
+    s.set_atoms(R, Z, 0.8)
+    vext = O.vext_gaussians(cfg, R, Z, 0.8)
+    tdt = torch.float64 if precision == 0 else torch.float32
+    Ud = dev(U, tdt)
+    out = torch.empty_like(Ud)
+    g = 1.0 / (2 * O.F_OCC * cfg.dV)
+    s.backward(Ud, g, out)
+    ref = O.apply_h(U, O.total_potential(O.density(U), vext, cfg), cfg)
+    tol = 1e-11 if precision == 0 else 2e-5
+    np.testing.assert_allclose(out.double().cpu().numpy(), ref, atol=tol * np.max(np.abs(ref)))
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_set_orbitals_orthonormalises(P, precision):
+    n, L, N = (24, 20, 16), (8.0, 7.0, 6.0), 5
+    R, Z, U = _system(n, L, N, 3, M=3)
+    cfg = ocfg(n, L, N)
+    s = solver(P, n, L, N, precision=precision)
+    s.set_atoms(R, Z, 0.8)
+    s.set_orbitals(U if precision == 0 else U.astype(np.float32))
+    Uin = U if precision == 0 else U.astype(np.float32).astype(np.float64)
+    W, _, _ = O.cholesky_qr(Uin, cfg)
+    vext = O.vext_gaussians(cfg, R, Z, 0.8)
+    tol = 1e-11 if precision == 0 else 3e-6
+    got = s.get_orbitals()
+    np.testing.assert_allclose(got, W, atol=tol * np.max(np.abs(W)))
+    rho = O.density(W)
+    np.testing.assert_allclose(s.get_density(), rho, atol=tol * np.max(rho))
+    Vref = O.total_potential(rho, vext, cfg)
+    np.testing.assert_allclose(s.get_potential(), Vref, atol=tol * np.max(np.abs(Vref)))
+    e = s.energy()
+    # the reported energy is that of the returned orbitals
+    ref = O.energy(got, vext, cfg)
+    assert abs(e["total"] - ref) < (1e-10 if precision == 0 else 1e-8) * max(1.0, abs(ref))
+    s.close()
+
+
+# ------------------------------------------------------------------ whole iteration, FP64
+def _workload_solver(P, name, precision=0, **kw):
+    w, R, Z, U0 = inputs.workload_inputs(name)
+    s = solver(P, w.n, w.L, w.N, order=w.order, precision=precision, **kw)
+    s.set_atoms(R, Z, w.width)
+    return w, R, Z, U0, s
+
+
+def test_fp64_trajectory_matches_oracle_l10_g32_n4(P):
+    """Workload L=10, 32^3, N=4, 200 steps: energies to 1e-8 Ha at every step."""
+    w, R, Z, U0, s = _workload_solver(P, "l10_g32_n4")
+    s.set_orbitals(U0)
+    rep = s.iterate(w.iterations)
+    assert rep["iterations"] == w.iterations
+    Eg, taug = s.history()
+    cfg = ocfg(w.n, w.L, w.N, order=w.order)
+    vext = O.vext_gaussians(cfg, R, Z, w.width)
+    st = O.run(U0, vext, cfg, w.iterations)
+    Eo = np.array([h.energy for h in st.history])
+    to = np.array([h.tau for h in st.history])
+    assert len(Eg) == len(Eo)
+    assert np.max(np.abs(Eg - Eo)) <= 1e-8, np.max(np.abs(Eg - Eo))
+    np.testing.assert_allclose(taug, to, rtol=1e-6)
+    assert rep["backtracks"] == sum(h.backtracks for h in st.history)
+    Wg = s.get_orbitals()
+    # same trajectory: orbitals, density and orthonormality as numbers
+    orb_err = np.max(np.abs(Wg - st.W))
+    rho_err = np.max(np.abs(s.get_density() - st.rho)) / np.max(st.rho)
+    ortho = np.max(np.abs(O.inner_matrix(Wg, Wg, cfg) - np.eye(w.N)))
+    assert orb_err < 1e-7 * np.max(np.abs(st.W)), orb_err
+    assert rho_err < 1e-8, rho_err
+    assert ortho < 1e-12, ortho
+    s.close()
+
+
+def test_iterate_in_chunks_equals_one_call(P):
+    w, R, Z, U0, s = _workload_solver(P, "l10_g32_n4")
+    s.set_orbitals(U0)
+    s.iterate(30)
+    s.iterate(1)
+    s.iterate(19)
+    E1, _ = s.history()
+    s.set_orbitals(U0)
+    s.iterate(50)
+    E2, _ = s.history()
+    assert np.array_equal(E1, E2)
+    s.close()
+
+
+def test_state_resume_is_bit_exact(P):
+    w, R, Z, U0, s = _workload_solver(P, "l10_g32_n4")
+    s.set_orbitals(U0)
+    s.iterate(40)
+    blob = s.get_state()
+    s.iterate(25)
+    E_ref, _ = s.history()
+    W_ref = s.get_orbitals()
+    s2 = solver(P, w.n, w.L, w.N, order=w.order)
+    s2.set_atoms(R, Z, w.width)
+    s2.set_state(blob)
+    s2.iterate(25)
+    E2, _ = s2.history()
+    assert np.array_equal(E_ref, E2)
+    assert np.array_equal(W_ref, s2.get_orbitals())
+    s.close()
+    s2.close()
+
+
+def test_energy_criterion_stops(P):
+    w, R, Z, U0, s = _workload_solver(P, "l10_g32_n4", bb_variant=3)
+    s.set_orbitals(U0)
+    rep = s.iterate(5000, e_tol=1e-11)
+    assert rep["converged"] == 1 and rep["status"] == P.OK
+    assert rep["df_mean3"] < 1e-11
+    s.close()
+
+
+# ------------------------------------------------------------------ a8: mixed precision
+def test_mixed_form_converges_to_fp64_energy(P):
+    """FP32 bulk + FP32 Gram/rotation with FP64 Cholesky/energies: |E32 - E64| <= 1e-6 Ha."""
+    res = {}
+    for prec in (0, 1):
+        w, R, Z, U0, s = _workload_solver(P, "l10_g32_n4", precision=prec, bb_variant=3)
+        s.set_orbitals(U0)
+        s.iterate(2500)
+        res[prec] = s.energy()["total"]
+        if prec == 1:
+            W = s.get_orbitals()
+            cfg = ocfg(w.n, w.L, w.N, order=w.order)
+            ortho = np.max(np.abs(O.inner_matrix(W, W, cfg) - np.eye(w.N)))
+            assert ortho < 2e-6, ortho
+            vext = O.vext_gaussians(cfg, R, Z, w.width)
+            # the reported energy is the energy of the returned FP32 orbitals
+            assert abs(O.energy(W, vext, cfg) - res[1]) < 1e-6
+        s.close()
+    assert abs(res[0] - res[1]) <= 1e-6, res
+
+
+# ------------------------------------------------------------------ a9: adjoint and forces
+@pytest.mark.parametrize("precision", [0, 1])
+def test_atom_gradients_match_oracle(P, precision):
+    n, L, N = (24, 20, 22), (7.0, 6.0, 6.5), 3
+    R, Z, U = _system(n, L, N, 17, M=3)
+    cfg = ocfg(n, L, N)
+    W, _, _ = O.cholesky_qr(U, cfg)
+    if precision == 1:
+        W = W.astype(np.float32).astype(np.float64)
+    s = solver(P, n, L, N, precision=precision)
+    s.set_atoms(R, Z, 0.8)
+    _, dR, dZ = s.backward(W, 1.0, None, atoms=True)
+    rR, rZ = O.energy_gradient_atoms(W, cfg, R, Z, 0.8)
+    tol = 1e-10 if precision == 0 else 1e-6
+    np.testing.assert_allclose(dR, rR, atol=tol * max(1.0, np.max(np.abs(rR))))
+    np.testing.assert_allclose(dZ, rZ, atol=tol * max(1.0, np.max(np.abs(rZ))))
+    s.close()
+
+
+def test_autograd_function_matches_oracle_and_fd(P):
+    from paper_1510_07230_gb300.autograd import kohn_sham_energy
+    n, L, N = (16, 14, 12), (6.0, 5.5, 5.0), 2
+    R, Z, U = _system(n, L, N, 23)
+    cfg = ocfg(n, L, N, order=4)
+    s = solver(P, n, L, N, order=4)
+    Ut = dev(0.3 * U).requires_grad_(True)
+    Rt = torch.tensor(R, dtype=torch.float64, requires_grad=True)
+    Zt = torch.tensor(Z, dtype=torch.float64, requires_grad=True)
+    E = kohn_sham_energy(Ut, Rt, Zt, s)
+    E.backward()
+    Un = 0.3 * U
+    vext = O.vext_gaussians(cfg, R, Z, 0.8)
+    assert abs(E.item() - O.energy(Un, vext, cfg)) < 1e-10
+    gU = O.energy_gradient_orbitals(Un, vext, cfg)
+    np.testing.assert_allclose(Ut.grad.cpu().numpy(), gU, atol=1e-11 * np.max(np.abs(gU)))
+    rR, rZ = O.energy_gradient_atoms(Un, cfg, R, Z, 0.8)
+    np.testing.assert_allclose(Rt.grad.numpy(), rR, atol=1e-10 * max(1, np.max(np.abs(rR))))
+    np.testing.assert_allclose(Zt.grad.numpy(), rZ, atol=1e-10 * max(1, np.max(np.abs(rZ))))
+    # central finite differences of the GPU energy itself (step 1e-4 bohr)
+    eps = 1e-4
+    for I, a in [(0, 0), (1, 2)]:
+        Rp, Rm = R.copy(), R.copy()
+        Rp[I, a] += eps
+        Rm[I, a] -= eps
+        s.set_atoms(Rp, Z, 0.8)
+        ep = s.evaluate(Un)["total"]
+        s.set_atoms(Rm, Z, 0.8)
+        em = s.evaluate(Un)["total"]
+        fd = (ep - em) / (2 * eps)
+        assert abs(fd - Rt.grad[I, a].item()) < 1e-6 * max(1.0, abs(fd))
+    s.close()
+
+
+# ------------------------------------------------------------------ failure statuses
+def test_rank_deficient_orbitals_report_not_spd(P):
+    n, L, N = 12, 5.0, 3
+    U = inputs.random_orbitals(1, N, (n, n, n))
+    U[2] = U[0]
+    s = solver(P, n, L, N)
+    with pytest.raises(P.PouError) as ei:
+        s.set_orbitals(U)
+    assert ei.value.status == P.ENOTSPD
+    s.set_orbitals(inputs.random_orbitals(2, N, (n, n, n)))  # the context stays usable
+    s.iterate(3)
+    s.close()
+
+
+def test_nan_potential_reports_enan(P):
+    n, L, N = 12, 5.0, 2
+    v = np.zeros((n, n, n))
+    v[3, 4, 5] = np.nan
+    s = solver(P, n, L, N)
+    s.set_vext(v)
+    with pytest.raises(P.PouError) as ei:
+        s.set_orbitals(inputs.random_orbitals(1, N, (n, n, n)))
+    assert ei.value.status == P.ENAN
+    s.close()
+
+
+def test_iterate_without_orbitals_is_einval(P):
+    s = solver(P, 12, 5.0, 2)
+    with pytest.raises(P.PouError) as ei:
+        s.iterate(1)
+    assert ei.value.status == P.EINVAL
+    s.close()
+
+
+# ------------------------------------------------------------------ edge cases
+def test_single_orbital_and_tiny_grid(P):
+    n, L, N = (5, 4, 6), (3.0, 2.5, 3.5), 1
+    R, Z, U = _system(n, L, N, 31, M=1)
+    cfg = ocfg(n, L, N, order=4)
+    vext = O.vext_gaussians(cfg, R, Z, 0.8)
+    s = solver(P, n, L, N, order=4)
+    s.set_atoms(R, Z, 0.8)
+    s.set_orbitals(U)
+    s.iterate(40)
+    st = O.run(U, vext, cfg, 40)
+    Eg, _ = s.history()
+    assert np.max(np.abs(Eg - np.array([h.energy for h in st.history]))) < 1e-9
+    s.close()
+
+
+def test_max_orbitals_128(P):
+    n, L, N = (24, 24, 24), (9.0,) * 3, 128
+    cfg = ocfg(n, L, N)
+    R, Z = inputs.atoms(77, 8, 9.0, "uniform26")
+    U = inputs.random_orbitals(77, N, cfg.n)
+    vext = O.vext_gaussians(cfg, R, Z, 0.8)
+    s = solver(P, n, L, N)
+    s.set_atoms(R, Z, 0.8)
+    s.set_orbitals(U)
+    s.iterate(3)
+    st = O.run(U, vext, cfg, 3)
+    Eg, _ = s.history()
+    assert np.max(np.abs(Eg - np.array([h.energy for h in st.history]))) < 1e-8
+    W = s.get_orbitals()
+    assert np.max(np.abs(O.inner_matrix(W, W, cfg) - np.eye(N))) < 1e-11
+    s.close()
+
+
+def test_device_orbitals_and_stream(P):
+    """Orbitals passed as CUDA tensors, on torch's current stream."""
+    w, R, Z, U0 = inputs.workload_inputs("l10_g32_n4")
+    st_ptr = torch.cuda.current_stream().cuda_stream
+    s = P.Solver(w.n, w.L, w.N, order=w.order, stream=st_ptr)
+    s.set_atoms(R, Z, w.width)
+    s.set_orbitals(dev(U0))
+    s.iterate(10)
+    out = torch.empty((w.N, w.n, w.n, w.n), dtype=torch.float32, device="cuda")
+    s.get_orbitals(out)
+    s2 = P.Solver(w.n, w.L, w.N, order=w.order)
+    s2.set_atoms(R, Z, w.width)
+    s2.set_orbitals(U0)
+    s2.iterate(10)
+    np.testing.assert_allclose(out.double().cpu().numpy(), s2.get_orbitals().astype(np.float32), atol=0)
+    assert s.launch_count() > 10 * 7
+    s.close()
+    s2.close()

@@ -85,6 +85,20 @@ def test_vext_periodic_images():
     assert abs(cfg.dV * V1.sum() + Z.sum() * (2 * math.pi * 0.64) ** 1.5) < 1e-6
 
 
+def test_vext_product_form_equals_literal_image_sum():
+    cfg = O.Config(n=(14, 12, 10), L=(6.0, 5.0, 4.5))
+    R = np.array([[0.2, 4.9, 2.0], [3.1, 2.2, 4.4], [5.8, 0.1, 0.05]])
+    Z = np.array([2.0, 5.5, 3.0])
+    np.testing.assert_allclose(O.vext_gaussians(cfg, R, Z, 0.8), O.vext_gaussians_literal(cfg, R, Z, 0.8),
+                               atol=1e-13)
+
+
+def test_random_orbitals_prefix_is_the_same_draw():
+    a = inputs.random_orbitals(4, 6, (5, 4, 3))
+    b = inputs.random_orbitals(4, 6, (5, 4, 3), count=2)
+    assert np.array_equal(a[:2], b)
+
+
 def test_hartree_cosine_closed_form():
     cfg = O.Config(n=(16, 12, 10), L=(7.0, 6.0, 5.0))
     x, y, z = O.grid_coords(cfg)
