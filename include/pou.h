@@ -79,7 +79,8 @@ typedef struct {
   int precision;      /* pou_precision */
   int hartree;        /* 1: Hartree term on; 0: off (closed-form tests) */
   int exchange;       /* 1: Slater exchange on; 0: off */
-  int bb_variant;     /* 1: tau1 = tr<S^T S>/|tr<S^T Y>|, 2: tau2, 3: alternate */
+  int bb_variant;     /* 1: tau1 = tr<S^T S>/|tr<S^T Y>|, 2: tau2 = |tr<S^T Y>|/tr<Y^T Y>,
+                         3 (default): tau1 on even steps l, tau2 on odd steps */
   double rho1;        /* backtracking constants of Eq. ene-de: 1e-4 */
   double delta;       /* 0.1 */
   double eta;         /* 0.85 */
@@ -88,7 +89,9 @@ typedef struct {
   double tau_min;     /* step clamp: 1e-12 */
   double tau_max;     /* step clamp: 1e3 */
   int n_org;          /* Algorithm M: Orth every n_org steps (only 1 is accepted) */
-  int n_diag;         /* Algorithm M: subspace diagonalisation period (only 0 = off) */
+  int n_diag;         /* Algorithm M: subspace diagonalisation every n_diag steps
+                         (Sec. 3.3: Sigma = <W^T H W>, P^T Sigma P diagonal, W <- W P);
+                         0 = off */
   void* stream;       /* cudaStream_t to run on; NULL: the library creates one */
 } pou_config;
 

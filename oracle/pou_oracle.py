@@ -32,6 +32,7 @@ diagonalisation; Sec. 3.2):
 4. Q^(l+1) = eta Q^l + 1, C^(l+1) = (eta Q^l C^l + E^(l+1)) / Q^(l+1)
 
 Readings where the paper is silent (also listed in the design notes):
+the two BB steps ("tau1 or tau2") alternate by default, tau1 on even l;
 tau at l = 0 and when tr<S^T Y> = 0 is 1 / lambda_max(-1/2 Lap_h); tau is
 clamped to [1e-12, 1e3]; after ``max_backtrack`` reductions the last trial
 is accepted and counted; the Hartree kernel is 4 pi / |G|^2 with G = 2 pi m / L,
@@ -63,7 +64,7 @@ class Config:
     N: int = 1
     hartree: int = 1
     exchange: int = 1
-    bb_variant: int = 1  # 1: tau1, 2: tau2, 3: alternate (tau1 on even l)
+    bb_variant: int = 3  # 1: tau1, 2: tau2, 3: alternate (tau1 on even l, tau2 on odd l)
     rho1: float = 1e-4  # Sec. 3.2 constants
     delta: float = 0.1
     eta: float = 0.85
@@ -316,6 +317,7 @@ class State:
     W_prev: Optional[np.ndarray] = None
     Z_prev: Optional[np.ndarray] = None
     tau_prev: float = 0.0
+    tau_next: Optional[float] = None
     history: List[IterRecord] = field(default_factory=list)
     df: List[float] = field(default_factory=list)
 
@@ -371,12 +373,15 @@ def iterate(st: State, vext: np.ndarray, cfg: Config, full_sigma: bool = False) 
     dV = cfg.dV
     znorm2 = dV * float(np.sum(Z * Z))
     tau0 = default_tau0(cfg)
-    if st.W_prev is None:
+    if st.tau_next is not None:
+        tau = st.tau_next  # computed before a subspace rotation (see subspace_diagonalise)
+        st.tau_next = None
+    elif st.W_prev is None:
         tau = tau0
     else:
         tau = bb_step(W - st.W_prev, Z - st.Z_prev, cfg, st.l)
-        if not math.isfinite(tau) or tau <= 0:
-            tau = tau0
+    if not math.isfinite(tau) or tau <= 0:
+        tau = tau0
     tau = min(max(tau, cfg.tau_min), cfg.tau_max)
 
     orth_step = (st.l % max(cfg.n_org, 1)) == 0
@@ -417,23 +422,28 @@ def iterate(st: State, vext: np.ndarray, cfg: Config, full_sigma: bool = False) 
     st.df.append(abs(E_old - En) / (abs(E_old) + 1.0))
     st.history.append(IterRecord(En, t, backtracks, forced, gram_off, znorm2))
     if cfg.n_diag > 0 and st.l % cfg.n_diag == 0:
-        subspace_diagonalise(st, cfg)
+        subspace_diagonalise(st, vext, cfg, full_sigma)
     return st
 
 
-def subspace_diagonalise(st: State, cfg: Config) -> None:
-    """Sec. 3.3: P^T Sigma P = Gamma, W <- W P (rho, H and E unchanged)."""
+def subspace_diagonalise(st: State, vext: np.ndarray, cfg: Config, full_sigma: bool = False) -> None:
+    """Sec. 3.3: P^T Sigma P = Gamma, W <- W P (rho, H and E unchanged).
+
+    Reading: the Barzilai-Borwein step of the next step is taken from S and Y
+    of the orbitals before the rotation, so it is computed here, first.  The
+    rotated orbitals then serve as W^(l) for the step after.
+    """
     W = st.W
     N = W.shape[0]
     HW = apply_h(W, st.V, cfg)
-    Sig = inner_matrix(HW, W, cfg)
+    Zn, _ = search_direction(W, HW, cfg, full=full_sigma)
+    st.tau_next = bb_step(W - st.W_prev, Zn - st.Z_prev, cfg, st.l)
+    Sig = inner_matrix(W, HW, cfg)
     Sig = 0.5 * (Sig + Sig.T)
     _, P = np.linalg.eigh(Sig)
     st.W = (P.T @ W.reshape(N, -1)).reshape(W.shape)
-    # the BB history refers to the old basis; rotate it consistently
-    if st.W_prev is not None:
-        st.W_prev = (P.T @ st.W_prev.reshape(N, -1)).reshape(W.shape)
-        st.Z_prev = (P.T @ st.Z_prev.reshape(N, -1)).reshape(W.shape)
+    st.W_prev = None
+    st.Z_prev = None
 
 
 def converged_df(df: List[float], e_tol: float) -> bool:

@@ -13,12 +13,14 @@ namespace {
 constexpr int CNT = 512;
 
 __global__ void __launch_bounds__(CNT) k_cholinv(const State* st_ro, State* st, const double* S,
-                                                  double* Rinv, int N, int* info, double piv_rel) {
+                                                  double* Rinv, int N, int* info, double piv_rel,
+                                                  double reorth_thr) {
   extern __shared__ double A[];  // [N][N+1]
   __shared__ int fail;
   __shared__ double offmax[CNT / 32];
   __shared__ double dmax;
   if (st_ro && st_ro->done) return;
+  if (reorth_thr < 0.0 && !(st_ro && st_ro->reorth)) return;  // gated second pass
   const int ld = N + 1;
   const int tid = threadIdx.x;
   double om = 0.0;
@@ -36,11 +38,15 @@ __global__ void __launch_bounds__(CNT) k_cholinv(const State* st_ro, State* st, 
     double m = 0.0;
     for (int k = 0; k < N; ++k) m = fmax(m, fabs(A[k * ld + k]));
     dmax = m;
-    if (st) {
+    if (st && reorth_thr >= 0.0) {
       double o = 0.0;
       for (int w = 0; w < CNT / 32; ++w) o = fmax(o, offmax[w]);
       st->gram_off_trial = o;
+      // an ill-conditioned trial block loses orthogonality in the FP32 form:
+      // ask for a second Cholesky-QR pass
+      st->reorth = (reorth_thr > 0.0 && o > reorth_thr) ? 1 : 0;
     }
+    if (st && reorth_thr < 0.0) st->reorth_count += 1;
   }
   __syncthreads();
 
@@ -121,10 +127,10 @@ void configure_cholinv() {
 }
 
 void launch_cholinv(const State* st, const double* S, double* Rinv, int N, int* info, State* st_rw,
-                    double piv_rel, cudaStream_t s) {
+                    double piv_rel, double reorth_thr, cudaStream_t s) {
   const size_t smem = cholinv_smem_bytes(N);
   prof_begin("cholinv", s);
-  k_cholinv<<<1, CNT, smem, s>>>(st, st_rw, S, Rinv, N, info, piv_rel);
+  k_cholinv<<<1, CNT, smem, s>>>(st, st_rw, S, Rinv, N, info, piv_rel, reorth_thr);
   prof_end(s);
 }
 

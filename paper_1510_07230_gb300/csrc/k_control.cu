@@ -38,17 +38,23 @@ __global__ void __launch_bounds__(KNT) k_control(CtrlArgs a) {
   __shared__ double esum[NE];
   State* st = a.st;
   if (st->done) return;
+  if (a.refresh && !st->diag_now) return;
   const int cur = st->cur;
-  const int t = 1 - cur;
+  // refresh: the rotated current pair's own sums; otherwise the trial's
+  const int t = a.refresh ? cur : 1 - cur;
   const int N = a.N;
   const int tid = threadIdx.x;
   double* part = a.part[t];
-  // per-orbital sums over tiles (fixed order)
+  // per-orbital sums over tiles (fixed order), and the sigma' they refer to
   for (int idx = tid; idx < N * NP; idx += KNT) {
     const int i = idx / NP, k = idx % NP;
-    const double* src = a.tilepart + (i64)i * a.ntile * NP + k;
+    if (k == P_SIGP) {
+      part[idx] = a.init ? 0.0 : a.sigma[cur][i];  // refresh: the eigenvalue
+      continue;
+    }
+    const double* src = a.tilepart + (i64)i * a.ntile * NPT + k;
     double s = 0.0;
-    for (int j = 0; j < a.ntile; ++j) s += src[(i64)j * NP];
+    for (int j = 0; j < a.ntile; ++j) s += src[(i64)j * NPT];
     part[idx] = s;
   }
   if (tid < NE) {
@@ -59,18 +65,22 @@ __global__ void __launch_bounds__(KNT) k_control(CtrlArgs a) {
   __syncthreads();
   const double dV = a.dV;
   double kin = 0.0, ss = 0.0, sy = 0.0, yy = 0.0, zz = 0.0;
+  __syncthreads();  // part[] complete (P_SIGP reads sigma[cur] before sigma[t] is written)
   for (int i = tid; i < N; i += KNT) {
     const double* p = part + i * NP;
     const double sig = dV * p[P_HW];
-    a.sigma[t][i] = sig;
-    kin += p[P_KIN];
-    zz += p[P_HH] - 2.0 * sig * p[P_HW] + sig * sig * p[P_WW];
-    if (!a.init) {
-      const double ds = sig - a.sigma[cur][i];
+    const double sigp = p[P_SIGP];
+    // ||z||^2 with z = hw - sigma w = z' - (sigma - sigma') w
+    const double dz = sig - sigp;
+    zz += p[P_ZZ] - 2.0 * dz * p[P_ZW] + dz * dz * p[P_WW];
+    kin += a.kc[0] * p[P_KX] + a.kc[1] * p[P_KY] + a.kc[2] * p[P_KZ];
+    if (!a.init && !a.refresh) {
+      const double ds = sig - sigp;
       ss += p[P_SS];
       sy += p[P_SB] - ds * p[P_SW];
       yy += p[P_BB] - 2.0 * ds * p[P_BW] + ds * ds * p[P_WW];
     }
+    a.sigma[t][i] = sig;
   }
   kin = block_sum(kin, sh);
   zz = block_sum(zz, sh);
@@ -78,6 +88,13 @@ __global__ void __launch_bounds__(KNT) k_control(CtrlArgs a) {
   sy = block_sum(sy, sh);
   yy = block_sum(yy, sh);
   if (tid != 0) return;
+  if (a.refresh) {
+    // rho, V and E are unchanged by a rotation within the span
+    st->znorm2 = zz * dV;
+    st->diag_now = 0;
+    st->diag_count += 1;
+    return;
+  }
 
   const double ekin = F_OCC * dV * kin;
   const double eext = dV * esum[E_EXT];
@@ -113,6 +130,9 @@ __global__ void __launch_bounds__(KNT) k_control(CtrlArgs a) {
     st->df[0] = st->df[1] = st->df[2] = 0.0;
     st->gram_off_acc = 0.0;
     st->converged = 0;
+    st->reorth_count = 0;
+    st->diag_now = 0;
+    st->diag_count = 0;
     st->done = 1;
     return;
   }
@@ -156,6 +176,8 @@ __global__ void __launch_bounds__(KNT) k_control(CtrlArgs a) {
   st->tau_bb = tau;
   st->tau_trial = tau;
   st->s = 0;
+  // Algorithm M: subspace diagonalisation every n_diag steps, before the next trial
+  st->diag_now = (a.n_diag > 0 && st->l % a.n_diag == 0) ? 1 : 0;
   if (st->l >= st->target_l) st->done = 1;
   if (st->e_tol > 0.0 && st->n_df >= 3 && (st->df[0] + st->df[1] + st->df[2]) / 3.0 < st->e_tol) {
     st->converged = 1;

@@ -138,6 +138,8 @@ struct FftArgs {
   double* V64_sel[2];
   float* V32_sel[2];
   double* Vd_sel[2];
+  float* dv32;           // iteration mode: V_new - V64[cur] (working type float)
+  double* dv64;          // (working type double)
 };
 
 // MODE: 0 x-forward from real rho, 1 y-forward, 2 z-forward+scale+inverse,
@@ -255,6 +257,11 @@ __global__ void __launch_bounds__(FNT) k_fft(FftArgs a) {
     const double V = ve + (a.hartree ? vh : 0.0) + vx;
     V64[g] = V;
     if (V32) V32[g] = (float)V;
+    if (a.st) {
+      const double d = V - a.V64_sel[a.st->cur][g];
+      if (a.dv32) a.dv32[g] = (float)d;
+      if (a.dv64) a.dv64[g] = d;
+    }
     s_ext += r * ve;
     s_h += r * vh;
     s_x += ex;
@@ -306,6 +313,11 @@ __global__ void __launch_bounds__(FNT) k_potential_local(FftArgs a, i64 ng) {
     const double V = ve + vx;
     V64[g] = V;
     if (V32) V32[g] = (float)V;
+    if (a.st) {
+      const double d = V - a.V64_sel[a.st->cur][g];
+      if (a.dv32) a.dv32[g] = (float)d;
+      if (a.dv64) a.dv64[g] = d;
+    }
     s_ext += r * ve;
     s_x += ex;
   }
@@ -377,7 +389,9 @@ int fft_plan_create(FftPlan* p, const int n[3], const double L[3]) {
     p->n[a] = n[a];
     p->nst[a] = factorize(n[a], p->radix[a]);
     if (p->nst[a] < 0) return -1;
-    total += 3 * (size_t)n[a];  // 2 doubles of twiddles + 1 of g^2
+    // per axis: n complex twiddles (2n doubles) then n values of g^2, each
+    // table starting on a 16-byte boundary (twiddles are read as double2)
+    total += 2 * (size_t)n[a] + (((size_t)n[a] + 1) & ~(size_t)1);
     // lines per block: keep two buffers within ~96 KB
     int lb = 16;
     while (lb > 1 && 2 * (size_t)lb * (n[a] + 1) * sizeof(double2) > 96 * 1024) lb /= 2;
@@ -400,8 +414,10 @@ int fft_plan_create(FftPlan* p, const int n[3], const double L[3]) {
       const double g = 2.0 * M_PI * (double)m / L[a];
       host[off + k] = g * g;
     }
-    off += (size_t)n[a];
+    off += ((size_t)n[a] + 1) & ~(size_t)1;
   }
+  for (int a = 0; a < 3; ++a)
+    if (offs_tw[a] % 2 != 0) return -4;  // a double2 table must be 16-byte aligned
   if (cudaMalloc(&p->mem, total * sizeof(double)) != cudaSuccess) return -2;
   if (cudaMemcpy(p->mem, host.data(), total * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
     return -3;
@@ -450,6 +466,9 @@ int launch_potential(const FftPlan& p, const PotArgs<T>& pa, cudaStream_t s) {
     for (int t = 0; t < 2; ++t)
       if (pa.V[t]) a.V64_sel[t] = reinterpret_cast<double*>(pa.V[t]);
     if (pa.V_x) a.V64 = reinterpret_cast<double*>(pa.V_x);
+    a.dv64 = reinterpret_cast<double*>(pa.dv_out);
+  } else {
+    a.dv32 = reinterpret_cast<float*>(pa.dv_out);
   }
   if (!pa.hartree && !pa.vh_out) {
     const int nblk = 152 * 4;

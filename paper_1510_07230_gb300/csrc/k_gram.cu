@@ -31,14 +31,47 @@ struct GT<double> {
 
 constexpr int GNT = 256;
 
-__device__ __forceinline__ void tri_index(int t, int* ti, int* tj) {
-  int r = 0, rem = t;
-  while (rem >= 16 - r) {
-    rem -= 16 - r;
-    ++r;
-  }
-  *ti = r;
-  *tj = r + rem;
+// Double-float accumulation in FP32 for sums of squares: (s, c) carries the
+// running sum s and its rounding error c.  x*x is split exactly into
+// p + e (FMA), and each addition s + p is split exactly into t + err
+// (TwoSum), so s + c is the sum to about 2^-44 relative.
+struct F2 {
+  float s, c;
+};
+__device__ __forceinline__ void two_sum_add(F2& a, float b, float extra) {
+  const float t = a.s + b;
+  const float bp = t - a.s;
+  const float err = (a.s - (t - bp)) + (b - bp);
+  a.c += err + extra;
+  a.s = t;
+}
+__device__ __forceinline__ void add_square(F2& a, float x) {
+  const float p = x * x;
+  two_sum_add(a, p, fmaf(x, x, -p));
+}
+__device__ __forceinline__ void add_f2(F2& a, const F2& b) { two_sum_add(a, b.s, b.c); }
+
+// SplitMix64 output function (Steele, Lea and Flood, 2014), used as a
+// counter-based source of uniform bits.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+
+// t + r rounded to FP32 without bias: with d the exact residual of the
+// nearest rounding s, the neighbour on d's side is chosen with probability
+// |d| / ulp, so the expected stored value is t + r.  Near convergence the
+// corrections that keep an orbital normalised are below half an ulp of every
+// element, and round-to-nearest would drop them all the same way.
+__device__ __forceinline__ float round_unbiased(float t, float r, unsigned long long key) {
+  const float s = t + r;
+  const float d = (t - s) + r;  // exact when |t| >= |r|
+  if (d == 0.f) return s;
+  const float nb = nextafterf(s, d > 0.f ? INFINITY : -INFINITY);
+  const float prob = d / (nb - s);
+  const float u = (float)(mix64(key) >> 40) * (1.0f / 16777216.0f);
+  return u < prob ? nb : s;
 }
 
 template <typename T>
@@ -47,15 +80,25 @@ __device__ __forceinline__ T trial_value(const T* W, const T* H, T coef, T tau, 
   return coef * W[off] - tau * H[off];
 }
 
+// Gram of a block over the grid dimension.  Work unit: a tile of BK
+// consecutive grid points; CTA b of G takes tiles b, b + G, b + 2G, ...
+// spread over the whole grid, so that its running sums of off-diagonal
+// products stay incoherent (small) instead of accumulating one region's
+// overlap.  Sums are two-level: a per-tile partial (lo) is added into a
+// per-CTA total (hi).  The next tile is prefetched into registers while the
+// current one is multiplied out of shared memory (double buffer, one barrier
+// per tile).  Every thread owns an RT x RT block of the ST x ST super-tile.
 template <typename T>
-__global__ void __launch_bounds__(GNT) k_gram(GramArgs<T> a, i64 chunk, int nsup, int npair) {
+__global__ void __launch_bounds__(GNT, 1) k_gram(GramArgs<T> a, i64 ntiles, int nsup, int npair) {
   constexpr int RT = GT<T>::RT, ST = GT<T>::ST, BK = GT<T>::BK;
-  __shared__ __align__(16) T As[BK][ST + 4];
-  __shared__ __align__(16) T Bs[BK][ST + 4];
+  constexpr int PER = ST * BK / GNT;  // tile elements loaded per thread
+  __shared__ __align__(16) T As[2][BK][ST + 4];
+  __shared__ __align__(16) T Bs[2][BK][ST + 4];
   __shared__ T coefs[ST], coefs2[ST];
 
   if (a.st && a.st->done) return;
-  const bool general = (a.B != nullptr);
+  if (!gate_open(a.st, a.gate)) return;
+  const bool general = (a.B != nullptr) || a.src_cur_pair;
   const int p = blockIdx.y;
   int I, J;
   if (general) {
@@ -72,22 +115,9 @@ __global__ void __launch_bounds__(GNT) k_gram(GramArgs<T> a, i64 chunk, int nsup
   }
   const bool diag = (!general) && (I == J);
   const int tid = threadIdx.x;
-  int ti = 0, tj = 0;
-  bool active = true;
-  if (diag) {
-    if (tid < 136)
-      tri_index(tid, &ti, &tj);
-    else
-      active = false;
-  } else {
-    ti = tid / 16;
-    tj = tid % 16;
-  }
-
+  const int ti = tid / 16, tj = tid % 16;
   const i64 ng = a.ng;
   const int N = a.N;
-  const i64 k0 = (i64)blockIdx.x * chunk;
-  const i64 k1 = min(ng, k0 + chunk);
 
   const T* Wa;
   const T* Ha = nullptr;
@@ -105,68 +135,101 @@ __global__ void __launch_bounds__(GNT) k_gram(GramArgs<T> a, i64 chunk, int nsup
       coefs[r] = gi < N ? (T)(1.0 + tau * a.sigma[cur][gi]) : T(0);
       coefs2[r] = gj < N ? (T)(1.0 + tau * a.sigma[cur][gj]) : T(0);
     }
+  } else if (a.src_trial_slot) {
+    Wa = a.W[1 - a.st->cur];
+    Bsrc = Wa;
+  } else if (a.src_cur_pair) {
+    Wa = a.W[a.st->cur];
+    Bsrc = a.HW[a.st->cur];
   } else {
     Wa = a.A;
     Bsrc = general ? a.B : a.A;
   }
   __syncthreads();
 
-  T acc[RT][RT];
+  // element e of a tile: row r = e / BK (orbital within the super-tile), k = e % BK
+  T pa[PER], pah[PER], pb[PER], pbh[PER];
+  auto fetch = [&](i64 tile) {
+    const i64 k0 = tile * BK;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = tid + q * GNT;
+      const int r = e / BK, k = e % BK;
+      const int gi = I * ST + r, gj = J * ST + r;
+      const i64 gk = k0 + k;
+      const bool okA = gi < N && gk < ng, okB = gj < N && gk < ng;
+      pa[q] = okA ? Wa[(i64)gi * ng + gk] : T(0);
+      if (a.trial) pah[q] = okA ? Ha[(i64)gi * ng + gk] : T(0);
+      if (!diag) {
+        pb[q] = okB ? Bsrc[(i64)gj * ng + gk] : T(0);
+        if (a.trial) pbh[q] = okB ? Ha[(i64)gj * ng + gk] : T(0);
+      }
+    }
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = tid + q * GNT;
+      const int r = e / BK, k = e % BK;
+      As[buf][k][r] = a.trial ? coefs[r] * pa[q] - tauT * pah[q] : pa[q];
+      if (!diag) Bs[buf][k][r] = a.trial ? coefs2[r] * pb[q] - tauT * pbh[q] : pb[q];
+    }
+  };
+
+  T hi[RT][RT], lo[RT][RT];
 #pragma unroll
   for (int r = 0; r < RT; ++r)
 #pragma unroll
-    for (int c = 0; c < RT; ++c) acc[r][c] = T(0);
+    for (int c = 0; c < RT; ++c) hi[r][c] = T(0);
 
-  for (i64 kk = k0; kk < k1; kk += BK) {
-    for (int idx = tid; idx < ST * BK; idx += GNT) {
-      const int r = idx / BK, k = idx % BK;
-      const int gi = I * ST + r;
-      const i64 gk = kk + k;
-      T v = T(0);
-      if (gi < N && gk < k1) {
-        const i64 off = (i64)gi * ng + gk;
-        v = a.trial ? trial_value(Wa, Ha, coefs[r], tauT, off) : Wa[off];
-      }
-      As[k][r] = v;
-      if (!diag) {
-        const int gj = J * ST + r;
-        T u = T(0);
-        if (gj < N && gk < k1) {
-          const i64 off = (i64)gj * ng + gk;
-          u = a.trial ? trial_value(Wa, Ha, coefs2[r], tauT, off) : Bsrc[off];
-        }
-        Bs[k][r] = u;
-      }
-    }
-    __syncthreads();
-    if (active) {
-      const T(*Bt)[ST + 4] = diag ? As : Bs;
+  const i64 G = gridDim.x;
+  i64 t = blockIdx.x;
+  int buf = 0;
+  if (t < ntiles) {
+    fetch(t);
+    stash(0);
+  }
+  __syncthreads();
+  for (; t < ntiles; t += G) {
+    const i64 tn = t + G;
+    if (tn < ntiles) fetch(tn);
+    const T(*At)[ST + 4] = As[buf];
+    const T(*Bt)[ST + 4] = diag ? As[buf] : Bs[buf];
+#pragma unroll
+    for (int r = 0; r < RT; ++r)
+#pragma unroll
+      for (int c = 0; c < RT; ++c) lo[r][c] = T(0);
 #pragma unroll 4
-      for (int k = 0; k < BK; ++k) {
-        T av[RT], bv[RT];
+    for (int k = 0; k < BK; ++k) {
+      T av[RT], bv[RT];
 #pragma unroll
-        for (int r = 0; r < RT; ++r) av[r] = As[k][ti * RT + r];
+      for (int r = 0; r < RT; ++r) av[r] = At[k][ti * RT + r];
 #pragma unroll
-        for (int c = 0; c < RT; ++c) bv[c] = Bt[k][tj * RT + c];
+      for (int c = 0; c < RT; ++c) bv[c] = Bt[k][tj * RT + c];
 #pragma unroll
-        for (int r = 0; r < RT; ++r)
+      for (int r = 0; r < RT; ++r)
 #pragma unroll
-          for (int c = 0; c < RT; ++c) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
-      }
+        for (int c = 0; c < RT; ++c) lo[r][c] = fma(av[r], bv[c], lo[r][c]);
     }
+#pragma unroll
+    for (int r = 0; r < RT; ++r)
+#pragma unroll
+      for (int c = 0; c < RT; ++c) hi[r][c] += lo[r][c];
+    if (tn < ntiles) stash(buf ^ 1);
     __syncthreads();
+    buf ^= 1;
   }
 
-  if (!active) return;
   double* out = a.split + ((i64)blockIdx.x * npair + p) * (i64)(ST * ST);
 #pragma unroll
   for (int r = 0; r < RT; ++r)
 #pragma unroll
-    for (int c = 0; c < RT; ++c) out[(ti * RT + r) * ST + tj * RT + c] = (double)acc[r][c];
+    for (int c = 0; c < RT; ++c) out[(ti * RT + r) * ST + tj * RT + c] = (double)hi[r][c];
 }
 
 __global__ void k_gram_reduce(GramReduceArgs a) {
   if (a.st && a.st->done) return;
+  if (!gate_open(a.st, a.gate)) return;
   const int r = blockIdx.y * blockDim.y + threadIdx.y;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int N = a.N;
@@ -187,8 +250,11 @@ __global__ void k_gram_reduce(GramReduceArgs a) {
   for (int k = 0; k < a.nsplit; ++k) s += a.split[off + k * stride];
   s *= a.dV;
   if (a.trial && r == c) {
-    // exact FP64 norm of the trial column from the H-apply sums of W[cur]:
-    // ||a w - tau hw||^2 = a^2 <w,w> - 2 a tau <w,hw> + tau^2 <hw,hw>
+    // FP64 norm of the trial column a w - t hw (a, t: the coefficients as the
+    // kernels round them) from the H-apply sums of W[cur]:
+    //   a w - t hw = w - t z_e,  z_e = hw - s_e w,  s_e = (a - 1) / t,
+    //   z_e = z' - d w with z' = hw - sigma' w, d = s_e - sigma',
+    //   ||w - t z_e||^2 = <w,w> - 2 t <w,z_e> + t^2 <z_e,z_e>.
     const int cur = a.st->cur;
     const double tau = a.st->tau_trial;
     double coef = 1.0 + tau * a.sigma[cur][r];
@@ -198,7 +264,17 @@ __global__ void k_gram_reduce(GramReduceArgs a) {
       t = (double)(float)tau;
     }
     const double* pp = a.part[cur] + (i64)r * NP;
-    s = a.dV * (coef * coef * pp[P_WW] - 2.0 * coef * t * pp[P_HW] + t * t * pp[P_HH]);
+    const double d = (coef - 1.0) / t - pp[P_SIGP];
+    const double wz = pp[P_ZW] - d * pp[P_WW];
+    const double zz = pp[P_ZZ] - 2.0 * d * pp[P_ZW] + d * d * pp[P_WW];
+    s = a.dV * (pp[P_WW] - 2.0 * t * wz + t * t * zz);
+  }
+  if (a.normpart && r == c) {
+    // column norms of the block, summed without cancellation by the
+    // rotation that produced it
+    double t = 0.0;
+    for (int k = 0; k < a.nnorm; ++k) t += a.normpart[(i64)k * N + r];
+    s = a.dV * t;
   }
   a.S[(i64)r * N + c] = s;
   if (!a.general) a.S[(i64)c * N + r] = s;
@@ -217,10 +293,15 @@ __global__ void __launch_bounds__(RNT) k_rotate(RotArgs<T> a, int nchunks) {
   T* Xs = Rs + NPAD * NPAD;                               // [NPAD][RP + 4]
   T* Rlo = Xs + NPAD * (RP + 4);                          // [NPAD] low part of the diagonal
   T* coefs = Rlo + NPAD;                                  // [NPAD]
-  float* rsum = reinterpret_cast<float*>(coefs + NPAD);   // [4][RP]
+  float* self = reinterpret_cast<float*>(coefs + NPAD);   // [4][NPAD]: A_hi, A_lo, B_hi, B_lo
   constexpr int XS = RP + 4;
+  // FP32 form: the self term of output j, A_j w_j - B_j h_j with FP64 A, B
+  // (trial: A = R_jj (1 + tau sigma_j), B = R_jj tau; otherwise A = R_jj, B = 0),
+  // is summed exactly with the off-diagonal part and stored by unbiased rounding.
+  constexpr bool kExactSelf = (sizeof(T) == 4);
 
   if (a.st && a.st->done) return;
+  if (!gate_open(a.st, a.gate)) return;
   const int tid = threadIdx.x;
   int cur = 0;
   const T* Wsrc;
@@ -239,9 +320,17 @@ __global__ void __launch_bounds__(RNT) k_rotate(RotArgs<T> a, int nchunks) {
     for (int i = tid; i < NPAD; i += RNT) coefs[i] = i < N ? (T)(1.0 + tau * a.sigma[cur][i]) : T(0);
   } else if (a.st) {
     cur = a.st->cur;
-    Wsrc = a.A;
-    out = a.Wout[1 - cur];
-    rho = a.rho[1 - cur];
+    // in-place second pass reads the block it overwrites: every chunk is
+    // staged in shared memory before any of its outputs is stored
+    if (a.src_cur_slot) {
+      Wsrc = a.Wout[cur];
+      out = a.Wout[cur];
+      rho = nullptr;  // a rotation within the span leaves rho unchanged
+    } else {
+      Wsrc = a.src_trial_slot ? a.Wout[1 - cur] : a.A;
+      out = a.Wout[1 - cur];
+      rho = a.rho[1 - cur];
+    }
   } else {
     Wsrc = a.A;
     out = a.B;
@@ -250,10 +339,28 @@ __global__ void __launch_bounds__(RNT) k_rotate(RotArgs<T> a, int nchunks) {
   for (int idx = tid; idx < NPAD * NPAD; idx += RNT) {
     const int i = idx / NPAD, j = idx % NPAD;
     const double v = (i < N && j < N) ? a.Rinv[(i64)i * N + j] : 0.0;
-    Rs[idx] = (T)v;
-    if (i == j) Rlo[i] = (T)(v - (double)(T)v);
+    Rs[idx] = (kExactSelf && i == j) ? T(0) : (T)v;
+    if (i == j) {
+      Rlo[i] = kExactSelf ? T(0) : (T)(v - (double)(T)v);
+      if (kExactSelf) {
+        double A = v, B = 0.0;
+        if (a.trial && i < N) {
+          const double tau = a.st->tau_trial;
+          A = v * (1.0 + tau * a.sigma[a.st->cur][i]);
+          B = v * tau;
+        }
+        const float ah = (float)A, bh = (float)B;
+        self[i] = ah;
+        self[NPAD + i] = (float)(A - (double)ah);
+        self[2 * NPAD + i] = bh;
+        self[3 * NPAD + i] = (float)(B - (double)bh);
+      }
+    }
   }
   __syncthreads();
+  // counter for the unbiased rounding: one stream per pass and per use
+  const unsigned long long seed =
+      ((unsigned long long)(a.st ? a.st->passes : 0) << 2 | (unsigned long long)a.sr_salt) * 0x9e3779b97f4a7c15ULL;
 
   const int lane = tid & 31, warp = tid >> 5;
   const int jw = warp & 3, pw = warp >> 2;
@@ -262,6 +369,10 @@ __global__ void __launch_bounds__(RNT) k_rotate(RotArgs<T> a, int nchunks) {
   const int pl0 = pw * 32 + pg * 4; // 4 points within the chunk
   const int imax = a.general ? N : min(N, j0 + 8);
   const i64 ng = a.ng;
+  // compensated (Kahan) per-CTA column norms, held by the pg == 0 lanes
+  float nh[8], nc[8];
+#pragma unroll
+  for (int jj = 0; jj < 8; ++jj) nh[jj] = nc[jj] = 0.f;
 
   for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const i64 p0 = (i64)ch * RP;
@@ -303,12 +414,47 @@ __global__ void __launch_bounds__(RNT) k_rotate(RotArgs<T> a, int nchunks) {
         for (int q = 0; q < 4; ++q) acc[jj][q] = fma(lo, Xs[j * XS + pl0 + q], acc[jj][q]);
       }
     }
-    // store and density
-    float sq[4] = {0.f, 0.f, 0.f, 0.f};
+    if (kExactSelf) {
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        const int j = j0 + jj;
+        if (j >= N) continue;
+        const float ah = self[j], al = self[NPAD + j], bh = self[2 * NPAD + j], bl = self[3 * NPAD + j];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const i64 gp = p0 + pl0 + q;
+          float wv = 0.f, hv = 0.f;
+          if (gp < ng) {
+            if (a.trial) {
+              wv = (float)Wsrc[(i64)j * ng + gp];
+              hv = (float)Hsrc[(i64)j * ng + gp];
+            } else {
+              wv = (float)Xs[j * XS + pl0 + q];
+            }
+          }
+          const float off = (float)acc[jj][q];
+          const float p1 = wv * ah, e1 = fmaf(wv, ah, -p1);
+          const float p2 = hv * bh, e2 = fmaf(hv, bh, -p2);
+          const float t = p1 - p2;
+          const float bp = t - p1;
+          const float et = (p1 - (t - bp)) + (-p2 - bp);
+          const float u = t + off;
+          const float bq = u - t;
+          const float eu = (t - (u - bq)) + (off - bq);
+          const float r = ((e1 - e2) + (et + eu)) + (wv * al - hv * bl);
+          acc[jj][q] = (T)round_unbiased(u, r, seed ^ (unsigned long long)((i64)j * ng + gp));
+        }
+      }
+    }
+    // store and density (FP32 form: double-float sums of squares)
+    F2 sq[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sq[q].s = sq[q].c = 0.f;
     double sqd[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
     for (int jj = 0; jj < 8; ++jj) {
       const int j = j0 + jj;
+      float col = 0.f;
       if (j < N) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -317,8 +463,18 @@ __global__ void __launch_bounds__(RNT) k_rotate(RotArgs<T> a, int nchunks) {
           if (sizeof(T) == 8)
             sqd[q] += (double)acc[jj][q] * (double)acc[jj][q];
           else
-            sq[q] += (float)acc[jj][q] * (float)acc[jj][q];
+            add_square(sq[q], (float)acc[jj][q]);
+          col = fmaf((float)acc[jj][q], (float)acc[jj][q], col);  // points past ng hold 0
         }
+      }
+      if (a.normpart) {
+        col += __shfl_xor_sync(0xffffffffu, col, 4);
+        col += __shfl_xor_sync(0xffffffffu, col, 8);
+        col += __shfl_xor_sync(0xffffffffu, col, 16);
+        const float y = col - nc[jj];
+        const float t = nh[jj] + y;
+        nc[jj] = (t - nh[jj]) - y;
+        nh[jj] = t;
       }
     }
     if (rho != nullptr) {
@@ -331,8 +487,12 @@ __global__ void __launch_bounds__(RNT) k_rotate(RotArgs<T> a, int nchunks) {
       } else {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          sq[q] += __shfl_xor_sync(0xffffffffu, sq[q], 1);
-          sq[q] += __shfl_xor_sync(0xffffffffu, sq[q], 2);
+          for (int o = 1; o <= 2; o <<= 1) {
+            F2 other;
+            other.s = __shfl_xor_sync(0xffffffffu, sq[q].s, o);
+            other.c = __shfl_xor_sync(0xffffffffu, sq[q].c, o);
+            add_f2(sq[q], other);
+          }
         }
       }
     }
@@ -342,7 +502,7 @@ __global__ void __launch_bounds__(RNT) k_rotate(RotArgs<T> a, int nchunks) {
       if (jg == 0) {
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-          dsum[jw * RP + pl0 + q] = (sizeof(T) == 8) ? sqd[q] : (double)sq[q];
+          dsum[jw * RP + pl0 + q] = (sizeof(T) == 8) ? sqd[q] : (double)sq[q].s + (double)sq[q].c;
       }
       __syncthreads();
       if (tid < RP) {
@@ -354,7 +514,13 @@ __global__ void __launch_bounds__(RNT) k_rotate(RotArgs<T> a, int nchunks) {
       }
       __syncthreads();
     }
-    (void)rsum;
+  }
+  if (a.normpart && pg == 0) {
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+      const int j = j0 + jj;
+      if (j < N) a.normpart[((i64)blockIdx.x * 2 + pw) * N + j] = (double)nh[jj] - (double)nc[jj];
+    }
   }
 }
 
@@ -362,18 +528,18 @@ template <typename T>
 __global__ void k_density(const T* U, i64 ng, int N, double* rho) {
   const i64 p = (i64)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= ng) return;
-  double s = 0.0;
-  int i = 0;
-  while (i < N) {
-    T part = T(0);
-    const int e = min(N, i + 8);
-    for (; i < e; ++i) {
-      const T v = U[(i64)i * ng + p];
-      part = fma(v, v, part);
+  if (sizeof(T) == 8) {
+    double s = 0.0;
+    for (int i = 0; i < N; ++i) {
+      const double v = (double)U[(i64)i * ng + p];
+      s = fma(v, v, s);
     }
-    s += (double)part;
+    rho[p] = F_OCC * s;
+  } else {
+    F2 s{0.f, 0.f};
+    for (int i = 0; i < N; ++i) add_square(s, (float)U[(i64)i * ng + p]);
+    rho[p] = F_OCC * ((double)s.s + (double)s.c);
   }
-  rho[p] = F_OCC * s;
 }
 
 __global__ void k_f64_to_f32(const double* in, float* out, i64 n) {
@@ -411,14 +577,13 @@ void gram_layout(i64 ng, int N, bool general, int* nsplit, int* npair, i64* chun
   const int ST = GT<T>::ST, BK = GT<T>::BK;
   const int nsup = (N + ST - 1) / ST;
   const int np = general ? nsup * nsup : nsup * (nsup + 1) / 2;
-  const i64 target = (4 * 152 + np - 1) / np;
-  i64 c = (ng + target - 1) / target;
-  c = ((c + BK - 1) / BK) * BK;
-  c = std::max<i64>(c, 1024);
-  c = std::min<i64>(c, 16384);
+  const i64 ntiles = (ng + BK - 1) / BK;
+  // one CTA per SM in total, at least 32 tiles per CTA
+  i64 g = (152 + np - 1) / np;
+  g = std::max<i64>(1, std::min<i64>(g, ntiles / 32));
   *npair = np;
-  *chunk = c;
-  *nsplit = (int)((ng + c - 1) / c);
+  *chunk = ntiles;  // tiles over the whole grid
+  *nsplit = (int)g;
 }
 template void gram_layout<float>(i64, int, bool, int*, int*, i64*);
 template void gram_layout<double>(i64, int, bool, int*, int*, i64*);
@@ -426,12 +591,12 @@ template void gram_layout<double>(i64, int, bool, int*, int*, i64*);
 template <typename T>
 void launch_gram(const GramArgs<T>& a, cudaStream_t s) {
   int nsplit, npair;
-  i64 chunk;
-  gram_layout<T>(a.ng, a.N, a.B != nullptr, &nsplit, &npair, &chunk);
+  i64 ntiles;
+  gram_layout<T>(a.ng, a.N, a.B != nullptr || a.src_cur_pair, &nsplit, &npair, &ntiles);
   const int nsup = (a.N + GT<T>::ST - 1) / GT<T>::ST;
   dim3 grid(nsplit, npair);
   prof_begin("gram", s);
-  k_gram<T><<<grid, GNT, 0, s>>>(a, chunk, nsup, npair);
+  k_gram<T><<<grid, GNT, 0, s>>>(a, ntiles, nsup, npair);
   prof_end(s);
 }
 template void launch_gram<float>(const GramArgs<float>&, cudaStream_t);
@@ -448,7 +613,7 @@ void launch_gram_reduce(const GramReduceArgs& a, cudaStream_t s) {
 template <typename T>
 static size_t rotate_smem() {
   const int NPAD = 128;
-  return sizeof(T) * ((size_t)NPAD * NPAD + (size_t)NPAD * (RP + 4) + 2 * NPAD) + sizeof(float) * 4 * RP;
+  return sizeof(T) * ((size_t)NPAD * NPAD + (size_t)NPAD * (RP + 4) + 2 * NPAD) + sizeof(float) * 4 * NPAD;
 }
 
 void configure_rotate() {
@@ -456,12 +621,17 @@ void configure_rotate() {
   cudaFuncSetAttribute(k_rotate<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rotate_smem<double>());
 }
 
+int rotate_grid(i64 ng, int elem_bytes) {
+  const int nchunks = (int)((ng + RP - 1) / RP);
+  const int per_sm = elem_bytes == 4 ? 2 : 1;
+  return std::min(nchunks, 152 * per_sm);
+}
+
 template <typename T>
 void launch_rotate(const RotArgs<T>& a, cudaStream_t s) {
   const size_t smem = rotate_smem<T>();
   const int nchunks = (int)((a.ng + RP - 1) / RP);
-  const int per_sm = sizeof(T) == 4 ? 2 : 1;
-  const int grid = std::min(nchunks, 152 * per_sm);
+  const int grid = rotate_grid(a.ng, (int)sizeof(T));
   prof_begin("rotate_density", s);
   k_rotate<T><<<grid, RNT, smem, s>>>(a, nchunks);
   prof_end(s);

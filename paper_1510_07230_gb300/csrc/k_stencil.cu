@@ -1,17 +1,24 @@
 // H-apply pass: HW = -1/2 Lap_h W + V W on a uniform periodic grid, fused
 // with the per-orbital sums the iteration needs (Sec. 3.2):
 //   sigma_ii = <H w_i, w_i>, the kinetic energy f <w_i, -1/2 Lap_h w_i>
-//   (Eq. energy), ||z_i||^2 and the Barzilai-Borwein traces against the
-//   current iterate (S = W - W', Y = Z - Z').
+//   (Eq. energy, kept per axis without the 1/h^2 factors), the sums of
+//   z' = hw - sigma' w, and the Barzilai-Borwein traces against the current
+//   iterate W' (S = W - W', Y = Z - Z').
+//
+// The gradient difference is formed from the step itself,
+//   hw - hw' = -1/2 Lap_h s + V s + (V - V') w',   s = w - w',
+// with V - V' formed from the FP64 potentials by the potential pass (once per
+// grid point), so that every operand is as small as the step: for tiny steps
+// an FP32 difference of two H-products would be all rounding noise.  HW' is
+// therefore never read.
 //
 // Layout: one orbital after another, [nz][ny][nx] each, x fastest.
-// One CTA = one orbital x a 32x8 tile in (x, y) x a chunk of z planes.  The
-// CTA sweeps z: each thread keeps its column's z-neighbours in a register
-// queue; the current plane plus an x/y halo of width R is staged in shared
-// memory (double-buffered, one barrier per plane).  Halo cells wrap
-// periodically.  Second differences are formed as sums of neighbour
-// differences, (u[+d] - u) + (u[-d] - u), which are exact in floating point
-// for smooth fields, so the FP32 form keeps the kinetic energy accurate.
+// One CTA = one orbital x a 32x8 (x, y) tile x a range of z planes.  Planes
+// stream through a shared-memory ring (cp.async, PF planes in flight): each
+// stage holds the plane of w (and w') with an x/y halo of width R (periodic
+// wrap), V and, with history, V - V'.  Each thread keeps its
+// column's z-neighbours in register queues.  Second differences are sums of
+// neighbour differences, (u[+d] - u) + (u[-d] - u), exact for smooth fields.
 #include "pou_internal.cuh"
 
 namespace pou {
@@ -24,20 +31,58 @@ namespace {
 constexpr int TX = 32;
 constexpr int TY = 8;
 constexpr int NT = TX * TY;
+constexpr int PF = 2;  // planes in flight beyond the one being consumed
 
 __device__ __forceinline__ int wrapi(int v, int n) {
   v %= n;
   return v < 0 ? v + n : v;
 }
 
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+template <typename T, int R>
+struct Stage {
+  T w[TY + 2 * R][TX + 2 * R];
+  T p[TY + 2 * R][TX + 2 * R];  // w' (history only)
+  T v[TY][TX];
+  T dv[TY][TX];  // V - V' (history only)
+};
+
+// Compensated (Kahan) running sum: the sums that enter the energy and the
+// Gram diagonal run over a whole z range per thread, where plain FP32
+// accumulation would cost about 1e-9 relative.
+template <typename T>
+struct Ksum {
+  T s, c;
+  __device__ __forceinline__ void add(T x) {
+    const T y = x - c;
+    const T t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 template <typename T, int R>
 __global__ void __launch_bounds__(NT) k_apply_h(ApplyArgs<T> a) {
-  __shared__ T plane[2][TY + 2 * R][TX + 2 * R];
-  __shared__ double red[NT / 32][NP];
+  constexpr int S = R + 2 + PF;  // ring: freed plane, computing plane .. arrived plane, in flight
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Stage<T, R>* ring = reinterpret_cast<Stage<T, R>*>(smem_raw);
+  __shared__ double red[NT / 32][NPT];
 
   if (a.st && a.st->done) return;
+  if (a.mode == 3 && !a.st->diag_now) return;
   const int cur = a.st ? a.st->cur : 0;
-  const int t = (a.mode == 2) ? 0 : 1 - cur;
+  const int t = (a.mode == 2) ? 0 : (a.mode == 3 ? cur : 1 - cur);
   const bool prev = (a.mode == 0);
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const i64 ng = (i64)nx * ny * nz;
@@ -46,8 +91,10 @@ __global__ void __launch_bounds__(NT) k_apply_h(ApplyArgs<T> a) {
   T* hw = a.HW[t] ? a.HW[t] + (i64)orb * ng : nullptr;
   const T* V = a.V[t];
   const T* wp = prev ? a.W[cur] + (i64)orb * ng : nullptr;
-  const T* hp = prev ? a.HW[cur] + (i64)orb * ng : nullptr;
-  const T sigp = prev ? (T)a.sigma[cur][orb] : T(0);
+  const T* dVp = prev ? a.dV : nullptr;
+  // sigma' the z' sums refer to: the reference iterate's (mode 0) or the
+  // eigenvalue of the rotated orbital (mode 3)
+  const T sigp = (prev || a.mode == 3) ? (T)a.sigma[cur][orb] : T(0);
 
   const int ntx = (nx + TX - 1) / TX;
   const int tx0 = (blockIdx.x % ntx) * TX;
@@ -61,12 +108,11 @@ __global__ void __launch_bounds__(NT) k_apply_h(ApplyArgs<T> a) {
   const bool act = (x < nx) && (y < ny);
   // every thread of the tile tracks its (wrapped) column so that tile cells
   // past the grid edge hold the periodic neighbours
-  const int xw = wrapi(x, nx), yw = wrapi(y, ny);
-  const i64 col = (i64)yw * nx + xw;
+  const i64 col = (i64)wrapi(y, ny) * nx + wrapi(x, nx);
   const i64 pl = (i64)nx * ny;
 
-  // halo cell owned by this thread (80*R cells per plane)
-  int hx = -1, hy = -1, sx = 0, sy = 0;
+  // halo cell owned by this thread (80 R cells per plane)
+  int hx = -1, hy = 0, sx = 0, sy = 0;
   if (tid < 2 * R * TY) {  // left / right columns
     const int side = tid / (R * TY), r = tid % (R * TY);
     const int row = r / R, d = r % R;
@@ -85,83 +131,169 @@ __global__ void __launch_bounds__(NT) k_apply_h(ApplyArgs<T> a) {
   }
   const i64 hcol = (hx >= 0) ? (i64)hy * nx + hx : 0;
 
-  T q[2 * R + 1];
-#pragma unroll
-  for (int j = 0; j < 2 * R; ++j) q[j] = w[(i64)wrapi(z0 - R + j, nz) * pl + col];
-
-  T acc[NP];
-#pragma unroll
-  for (int k = 0; k < NP; ++k) acc[k] = T(0);
-
-  const T c1 = (R == 1) ? T(1) : T(16) / T(12);
-  const T c2 = (R == 1) ? T(0) : T(-1) / T(12);
-
-  for (int z = z0; z < z1; ++z) {
-    q[2 * R] = w[(i64)wrapi(z + R, nz) * pl + col];
-    const T c = q[R];
-    T(*buf)[TX + 2 * R] = plane[z & 1];
-    buf[ly + R][lx + R] = c;
-    if (hx >= 0) buf[sy][sx] = w[(i64)z * pl + hcol];
-    __syncthreads();
-    if (act) {
-      const int cx = lx + R, cy = ly + R;
-      T dx1 = (buf[cy][cx + 1] - c) + (buf[cy][cx - 1] - c);
-      T dy1 = (buf[cy + 1][cx] - c) + (buf[cy - 1][cx] - c);
-      T dz1 = (q[R + 1] - c) + (q[R - 1] - c);
-      T lap;
-      if (R == 1) {
-        lap = a.ihx2 * dx1 + a.ihy2 * dy1 + a.ihz2 * dz1;
-      } else {
-        T dx2 = (buf[cy][cx + 2] - c) + (buf[cy][cx - 2] - c);
-        T dy2 = (buf[cy + 2][cx] - c) + (buf[cy - 2][cx] - c);
-        T dz2 = (q[R + 2] - c) + (q[R - 2] - c);
-        lap = a.ihx2 * (c1 * dx1 + c2 * dx2) + a.ihy2 * (c1 * dy1 + c2 * dy2) +
-              a.ihz2 * (c1 * dz1 + c2 * dz2);
-      }
-      const i64 idx = (i64)z * pl + col;
-      const T kin = T(-0.5) * lap;
-      const T h = kin + V[idx] * c;
-      if (hw) hw[idx] = a.out_scale * h;
-      acc[P_WW] += c * c;
-      acc[P_HW] += h * c;
-      acc[P_HH] += h * h;
-      acc[P_KIN] += c * kin;
+  // plane pa is needed for pa in [z0 - R, z1 + R); it lives in stage (pa - z0 + R) mod S
+  const int a_first = z0 - R, a_last = z1 + R;  // exclusive end
+  auto stage_of = [&](int pa) { return (pa - a_first) % S; };
+  auto issue = [&](int pa) {
+    if (pa < a_last) {
+      Stage<T, R>& g = ring[stage_of(pa)];
+      const i64 zo = (i64)wrapi(pa, nz) * pl;
+      cp_async<sizeof(T)>(&g.w[ly + R][lx + R], w + zo + col);
+      if (hx >= 0) cp_async<sizeof(T)>(&g.w[sy][sx], w + zo + hcol);
       if (prev) {
-        const T s = c - wp[idx];
-        const T b = (h - hp[idx]) - sigp * s;
-        acc[P_SS] += s * s;
-        acc[P_SB] += s * b;
-        acc[P_SW] += s * c;
-        acc[P_BB] += b * b;
-        acc[P_BW] += b * c;
+        cp_async<sizeof(T)>(&g.p[ly + R][lx + R], wp + zo + col);
+        if (hx >= 0) cp_async<sizeof(T)>(&g.p[sy][sx], wp + zo + hcol);
+      }
+      if (pa >= z0 && pa < z1) {
+        cp_async<sizeof(T)>(&g.v[ly][lx], V + zo + col);
+        if (prev) cp_async<sizeof(T)>(&g.dv[ly][lx], dVp + zo + col);
       }
     }
+    cp_commit();  // one group per plane, empty past the end
+  };
+
+  for (int pa = a_first; pa < a_first + PF + 1; ++pa) issue(pa);
+
+  T qw[2 * R + 1], qp[2 * R + 1];
 #pragma unroll
-    for (int j = 0; j < 2 * R; ++j) q[j] = q[j + 1];
+  for (int j = 0; j <= 2 * R; ++j) qw[j] = qp[j] = T(0);
+  T acc[NPT];
+#pragma unroll
+  for (int k = 0; k < NPT; ++k) acc[k] = T(0);
+  // compensated: P_WW, P_ZW, P_ZZ, P_KX, P_KY, P_KZ
+  Ksum<T> kww{T(0), T(0)}, kzw{T(0), T(0)}, kzz{T(0), T(0)}, kkx{T(0), T(0)}, kky{T(0), T(0)}, kkz{T(0), T(0)};
+  const T ihx2 = a.ihx2, ihy2 = a.ihy2, ihz2 = a.ihz2;
+
+  for (int pa = a_first; pa < a_last; ++pa) {
+    cp_wait<PF>();    // plane pa has landed (this thread's copies)
+    __syncthreads();  // ... everyone's; and plane pa - R - 1 is no longer read
+    issue(pa + PF + 1);
+    const Stage<T, R>& ga = ring[stage_of(pa)];
+    // shift the z queues and append the centre values of plane pa
+#pragma unroll
+    for (int j = 0; j < 2 * R; ++j) {
+      qw[j] = qw[j + 1];
+      qp[j] = qp[j + 1];
+    }
+    qw[2 * R] = ga.w[ly + R][lx + R];
+    qp[2 * R] = prev ? ga.p[ly + R][lx + R] : T(0);
+    const int z = pa - R;
+    if (z < z0 || !act) continue;
+    const Stage<T, R>& g = ring[stage_of(z)];
+    const int cx = lx + R, cy = ly + R;
+    const T c = qw[R];
+    // second differences of w along each axis, without 1/h^2 (order 4: 16 d1 - d2)
+    T ex, ey, ez;
+    {
+      const T dx1 = (g.w[cy][cx + 1] - c) + (g.w[cy][cx - 1] - c);
+      const T dy1 = (g.w[cy + 1][cx] - c) + (g.w[cy - 1][cx] - c);
+      const T dz1 = (qw[R + 1] - c) + (qw[R - 1] - c);
+      if (R == 1) {
+        ex = dx1;
+        ey = dy1;
+        ez = dz1;
+      } else {
+        const T dx2 = (g.w[cy][cx + 2] - c) + (g.w[cy][cx - 2] - c);
+        const T dy2 = (g.w[cy + 2][cx] - c) + (g.w[cy - 2][cx] - c);
+        const T dz2 = (qw[R + 2] - c) + (qw[R - 2] - c);
+        ex = T(16) * dx1 - dx2;
+        ey = T(16) * dy1 - dy2;
+        ez = T(16) * dz1 - dz2;
+      }
+    }
+    const i64 idx = (i64)z * pl + col;
+    const T lap = ihx2 * ex + ihy2 * ey + ihz2 * ez;
+    const T kin = T(-0.5) * lap;
+    const T vv = g.v[ly][lx];
+    const T h = kin + vv * c;
+    if (hw) hw[idx] = a.out_scale * h;
+    const T zp = h - sigp * c;
+    kww.add(c * c);
+    acc[P_HW] += h * c;
+    kzw.add(zp * c);
+    kzz.add(zp * zp);
+    kkx.add(c * ex);
+    kky.add(c * ey);
+    kkz.add(c * ez);
+    if (prev) {
+      // s = w - w' and H applied to it
+      const T sc = c - qp[R];
+      auto sv = [&](int yy, int xx) { return g.w[yy][xx] - g.p[yy][xx]; };
+      T fx, fy, fz;
+      {
+        const T sx1 = (sv(cy, cx + 1) - sc) + (sv(cy, cx - 1) - sc);
+        const T sy1 = (sv(cy + 1, cx) - sc) + (sv(cy - 1, cx) - sc);
+        const T sz1 = ((qw[R + 1] - qp[R + 1]) - sc) + ((qw[R - 1] - qp[R - 1]) - sc);
+        if (R == 1) {
+          fx = sx1;
+          fy = sy1;
+          fz = sz1;
+        } else {
+          const T sx2 = (sv(cy, cx + 2) - sc) + (sv(cy, cx - 2) - sc);
+          const T sy2 = (sv(cy + 2, cx) - sc) + (sv(cy - 2, cx) - sc);
+          const T sz2 = ((qw[R + 2] - qp[R + 2]) - sc) + ((qw[R - 2] - qp[R - 2]) - sc);
+          fx = T(16) * sx1 - sx2;
+          fy = T(16) * sy1 - sy2;
+          fz = T(16) * sz1 - sz2;
+        }
+      }
+      const T dvv = g.dv[ly][lx];
+      const T hs = T(-0.5) * (ihx2 * fx + ihy2 * fy + ihz2 * fz) + vv * sc + dvv * qp[R];
+      const T b = hs - sigp * sc;  // (hw - hw') - sigma' s
+      acc[P_SS] += sc * sc;
+      acc[P_SB] += sc * b;
+      acc[P_SW] += sc * c;
+      acc[P_BB] += b * b;
+      acc[P_BW] += b * c;
+    }
   }
+  cp_wait<0>();
 
   if (a.tilepart == nullptr) return;
   // block reduction of the sums, promoted to FP64 before combining threads
   const int lane = tid & 31, warp = tid >> 5;
+  double fin[NPT];
 #pragma unroll
-  for (int k = 0; k < NP; ++k) {
-    double v = (double)acc[k];
+  for (int k = 0; k < NPT; ++k) fin[k] = (double)acc[k];
+  fin[P_WW] = kww.value();
+  fin[P_ZW] = kzw.value();
+  fin[P_ZZ] = kzz.value();
+  fin[P_KX] = kkx.value();
+  fin[P_KY] = kky.value();
+  fin[P_KZ] = kkz.value();
+#pragma unroll
+  for (int k = 0; k < NPT; ++k) {
+    double v = fin[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) red[warp][k] = v;
   }
   __syncthreads();
-  if (tid < NP) {
+  if (tid < NPT) {
     double v = 0.0;
 #pragma unroll
     for (int wi = 0; wi < NT / 32; ++wi) v += red[wi][tid];
     const int ntile = gridDim.x * gridDim.y;
     const int tile = blockIdx.y * gridDim.x + blockIdx.x;
-    a.tilepart[((i64)orb * ntile + tile) * NP + tid] = v;
+    a.tilepart[((i64)orb * ntile + tile) * NPT + tid] = v;
   }
 }
 
+template <typename T, int R>
+size_t apply_smem() {
+  return sizeof(Stage<T, R>) * (size_t)(R + 2 + PF);
+}
+
 }  // namespace
+
+void configure_apply_h() {
+  cudaFuncSetAttribute(k_apply_h<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)apply_smem<float, 1>());
+  cudaFuncSetAttribute(k_apply_h<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)apply_smem<float, 2>());
+  cudaFuncSetAttribute(k_apply_h<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)apply_smem<double, 1>());
+  cudaFuncSetAttribute(k_apply_h<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)apply_smem<double, 2>());
+}
 
 int apply_h_ntile(int nx, int ny, int nz, int N, int* nzc_out) {
   const int ntx = (nx + TX - 1) / TX, nty = (ny + TY - 1) / TY;
@@ -183,9 +315,9 @@ void launch_apply_h(const ApplyArgs<T>& a0, int order, cudaStream_t s, int* ntil
   dim3 grid(ntx * nty, nzc, a.N), block(TX, TY);
   prof_begin("apply_h", s);
   if (order == 2)
-    k_apply_h<T, 1><<<grid, block, 0, s>>>(a);
+    k_apply_h<T, 1><<<grid, block, apply_smem<T, 1>(), s>>>(a);
   else
-    k_apply_h<T, 2><<<grid, block, 0, s>>>(a);
+    k_apply_h<T, 2><<<grid, block, apply_smem<T, 2>(), s>>>(a);
   prof_end(s);
   if (ntile_out) *ntile_out = ntile;
 }

@@ -116,6 +116,10 @@ struct pou_ctx {
   double* Rinv;
   double* split;
   size_t split_elems;
+  double* normpart;  // column norms written by the rotation (FP32 form)
+  int nnorm;
+  double* evec;      // eigenvector scratch of the subspace diagonalisation
+  void* dv;          // V(trial) - V(current), working type (written by the potential pass)
   State* st;
   double* hist_E;
   double* hist_tau;
@@ -219,10 +223,155 @@ T* tp(void* p) {
 // hundred ulps of the Gram's own precision.
 double pivot_tol(const pou_ctx* c) { return c->dt == 0 ? 1e-13 : 1e-6; }
 
+// FP32 form: a trial Gram matrix further than this from the identity is
+// orthonormalised a second time (its Cholesky-QR loses about
+// cond(S) * (FP32 Gram error) of orthogonality).  The FP64 form keeps the
+// single Cholesky-QR of the method.
+constexpr double kReorthThreshold = 0.02;
+double reorth_thr(const pou_ctx* c) { return c->dt == 1 ? kReorthThreshold : 0.0; }
+
+// Stencil scale applied in the working type, and the FP64 per-axis kinetic
+// coefficients: -1/2 Lap_h = -1/2 sum_a e_a / (h_a^2 [12 for order 4]).
+double stencil_scale(const pou_ctx* c, int a) {
+  const double h2 = c->h[a] * c->h[a];
+  return c->cfg.stencil_order == 2 ? 1.0 / h2 : 1.0 / (12.0 * h2);
+}
+
+// Second Cholesky-QR pass on the block just written to W[1-cur], gated on
+// st->reorth (FP32 form only).
+template <typename T>
+void enqueue_second_orth(pou_ctx* c) {
+  if (c->dt != 1) return;
+  cudaStream_t s = c->stream;
+  GramArgs<T> g{};
+  g.st = c->st;
+  for (int k = 0; k < 2; ++k) g.W[k] = tp<T>(c->W[k]);
+  g.src_trial_slot = 1;
+  g.gate = 1;
+  g.ng = c->ng;
+  g.N = c->N;
+  g.split = c->split;
+  launch_gram<T>(g, s);
+  int nsplit, npair;
+  i64 chunk;
+  gram_layout<T>(c->ng, c->N, false, &nsplit, &npair, &chunk);
+  GramReduceArgs r{};
+  r.st = c->st;
+  r.split = c->split;
+  r.nsplit = nsplit;
+  r.npair = npair;
+  r.ST = gram_supertile<T>();
+  r.N = c->N;
+  r.dV = c->dV;
+  r.S = c->S;
+  r.gate = 1;
+  r.normpart = c->normpart;
+  r.nnorm = c->nnorm;
+  launch_gram_reduce(r, s);
+  launch_cholinv(c->st, c->S, c->Rinv, c->N, nullptr, c->st, pivot_tol(c), -1.0, s);
+  RotArgs<T> ra{};
+  ra.st = c->st;
+  for (int k = 0; k < 2; ++k) {
+    ra.Wout[k] = tp<T>(c->W[k]);
+    ra.rho[k] = c->rho[k];
+  }
+  ra.Rinv = c->Rinv;
+  ra.src_trial_slot = 1;
+  ra.gate = 1;
+  ra.sr_salt = 1;
+  ra.ng = c->ng;
+  ra.N = c->N;
+  launch_rotate<T>(ra, s);
+}
+
+// Algorithm M, Sec. 3.3: when the controller has flagged it (State::diag_now),
+// Sigma = <W^T H W> of the current pair, P^T Sigma P = Gamma, W <- W P, and
+// HW and the per-orbital sums of the rotated pair are rebuilt.  Every kernel
+// is gated on the flag, so the sequence costs nothing on other steps.
+template <typename T>
+void enqueue_diag(pou_ctx* c) {
+  cudaStream_t s = c->stream;
+  GramArgs<T> g{};
+  g.st = c->st;
+  for (int k = 0; k < 2; ++k) {
+    g.W[k] = tp<T>(c->W[k]);
+    g.HW[k] = tp<T>(c->HW[k]);
+  }
+  g.src_cur_pair = 1;
+  g.gate = 2;
+  g.ng = c->ng;
+  g.N = c->N;
+  g.split = c->split;
+  launch_gram<T>(g, s);
+  int nsplit, npair;
+  i64 chunk;
+  gram_layout<T>(c->ng, c->N, true, &nsplit, &npair, &chunk);
+  GramReduceArgs r{};
+  r.st = c->st;
+  r.split = c->split;
+  r.nsplit = nsplit;
+  r.npair = npair;
+  r.ST = gram_supertile<T>();
+  r.N = c->N;
+  r.general = 1;
+  r.dV = c->dV;
+  r.S = c->S;
+  r.gate = 2;
+  launch_gram_reduce(r, s);
+  launch_eigh(c->st, c->S, c->Rinv, c->evec, c->sigma[0], c->sigma[1], c->N, s);
+  RotArgs<T> ra{};
+  ra.st = c->st;
+  for (int k = 0; k < 2; ++k) ra.Wout[k] = tp<T>(c->W[k]);
+  ra.Rinv = c->Rinv;
+  ra.src_cur_slot = 1;
+  ra.gate = 2;
+  ra.sr_salt = 2;
+  ra.general = 1;
+  ra.ng = c->ng;
+  ra.N = c->N;
+  launch_rotate<T>(ra, s);
+  ApplyArgs<T> aa{};
+  aa.st = c->st;
+  for (int k = 0; k < 2; ++k) {
+    aa.W[k] = tp<T>(c->W[k]);
+    aa.HW[k] = tp<T>(c->HW[k]);
+    aa.V[k] = tp<T>(c->V[k]);
+    aa.sigma[k] = c->sigma[k];
+  }
+  aa.mode = 3;
+  aa.tilepart = c->tilepart;
+  aa.out_scale = T(1);
+  aa.N = c->N;
+  aa.nx = c->nx;
+  aa.ny = c->ny;
+  aa.nz = c->nz;
+  aa.ihx2 = (T)stencil_scale(c, 0);
+  aa.ihy2 = (T)stencil_scale(c, 1);
+  aa.ihz2 = (T)stencil_scale(c, 2);
+  int ntile = 0;
+  launch_apply_h<T>(aa, c->cfg.stencil_order, s, &ntile);
+  CtrlArgs k{};
+  k.st = c->st;
+  for (int q = 0; q < 2; ++q) {
+    k.sigma[q] = c->sigma[q];
+    k.part[q] = c->part[q];
+  }
+  k.tilepart = c->tilepart;
+  k.ntile = ntile;
+  k.epart = c->epart;
+  k.neblk = 0;
+  k.N = c->N;
+  k.refresh = 1;
+  k.dV = c->dV;
+  for (int q = 0; q < 3; ++q) k.kc[q] = -0.5 * stencil_scale(c, q);
+  launch_control(k, s);
+}
+
 // ------------------------------------------------------------- one pass
 template <typename T>
 void enqueue_pass(pou_ctx* c) {
   cudaStream_t s = c->stream;
+  if (c->cfg.n_diag > 0) enqueue_diag<T>(c);
   // trial block Wt = W - tau Z from the current pair, Gram matrix
   GramArgs<T> g{};
   g.st = c->st;
@@ -254,10 +403,10 @@ void enqueue_pass(pou_ctx* c) {
     r.sigma[k] = c->sigma[k];
     r.part[k] = c->part[k];
   }
-  r.fp32_coef = (sizeof(T) == 4);
+  r.fp32_coef = 0;  // the rotation's self term uses the FP64 coefficients
   launch_gram_reduce(r, s);
   // Cholesky and R^-1 in FP64
-  launch_cholinv(c->st, c->S, c->Rinv, c->N, nullptr, c->st, pivot_tol(c), s);
+  launch_cholinv(c->st, c->S, c->Rinv, c->N, nullptr, c->st, pivot_tol(c), reorth_thr(c), s);
   // W_new = Wt R^-1 and rho into the other pair
   RotArgs<T> ra{};
   ra.st = c->st;
@@ -270,9 +419,11 @@ void enqueue_pass(pou_ctx* c) {
   }
   ra.Rinv = c->Rinv;
   ra.trial = 1;
+  ra.normpart = c->dt == 1 ? c->normpart : nullptr;
   ra.ng = c->ng;
   ra.N = c->N;
   launch_rotate<T>(ra, s);
+  enqueue_second_orth<T>(c);
   // Hartree potential, V and the energy sums of the trial density
   PotArgs<T> pa{};
   pa.st = c->st;
@@ -284,6 +435,7 @@ void enqueue_pass(pou_ctx* c) {
   pa.vext = c->vext;
   pa.work = c->work;
   pa.epart = c->epart;
+  pa.dv_out = tp<T>(c->dv);
   pa.hartree = c->cfg.hartree;
   pa.exchange = c->cfg.exchange;
   const int neblk = launch_potential<T>(c->fft, pa, s);
@@ -297,15 +449,16 @@ void enqueue_pass(pou_ctx* c) {
     aa.sigma[k] = c->sigma[k];
   }
   aa.mode = 0;
+  aa.dV = tp<T>(c->dv);
   aa.tilepart = c->tilepart;
   aa.out_scale = T(1);
   aa.N = c->N;
   aa.nx = c->nx;
   aa.ny = c->ny;
   aa.nz = c->nz;
-  aa.ihx2 = (T)(1.0 / (c->h[0] * c->h[0]));
-  aa.ihy2 = (T)(1.0 / (c->h[1] * c->h[1]));
-  aa.ihz2 = (T)(1.0 / (c->h[2] * c->h[2]));
+  aa.ihx2 = (T)stencil_scale(c, 0);
+  aa.ihy2 = (T)stencil_scale(c, 1);
+  aa.ihz2 = (T)stencil_scale(c, 2);
   int ntile = 0;
   launch_apply_h<T>(aa, c->cfg.stencil_order, s, &ntile);
   // accept / reject
@@ -332,6 +485,8 @@ void enqueue_pass(pou_ctx* c) {
   k.tau_max = c->cfg.tau_max;
   k.bb_variant = c->cfg.bb_variant;
   k.max_backtrack = c->cfg.max_backtrack;
+  k.n_diag = c->cfg.n_diag;
+  for (int q = 0; q < 3; ++q) k.kc[q] = -0.5 * stencil_scale(c, q);
   launch_control(k, s);
 }
 
@@ -362,7 +517,7 @@ pou_status init_from_staged(pou_ctx* c) {
   r.dV = c->dV;
   r.S = c->S;
   launch_gram_reduce(r, s);
-  launch_cholinv(c->st, c->S, c->Rinv, c->N, c->info, c->st, pivot_tol(c), s);
+  launch_cholinv(c->st, c->S, c->Rinv, c->N, c->info, c->st, pivot_tol(c), reorth_thr(c), s);
   RotArgs<T> ra{};
   ra.st = c->st;
   for (int k = 0; k < 2; ++k) {
@@ -372,9 +527,11 @@ pou_status init_from_staged(pou_ctx* c) {
   ra.A = tp<T>(c->W[0]);
   ra.Rinv = c->Rinv;
   ra.trial = 0;
+  ra.normpart = c->dt == 1 ? c->normpart : nullptr;
   ra.ng = c->ng;
   ra.N = c->N;
   launch_rotate<T>(ra, s);
+  enqueue_second_orth<T>(c);
   PotArgs<T> pa{};
   pa.st = c->st;
   for (int k = 0; k < 2; ++k) {
@@ -403,9 +560,9 @@ pou_status init_from_staged(pou_ctx* c) {
   aa.nx = c->nx;
   aa.ny = c->ny;
   aa.nz = c->nz;
-  aa.ihx2 = (T)(1.0 / (c->h[0] * c->h[0]));
-  aa.ihy2 = (T)(1.0 / (c->h[1] * c->h[1]));
-  aa.ihz2 = (T)(1.0 / (c->h[2] * c->h[2]));
+  aa.ihx2 = (T)stencil_scale(c, 0);
+  aa.ihy2 = (T)stencil_scale(c, 1);
+  aa.ihz2 = (T)stencil_scale(c, 2);
   int ntile = 0;
   launch_apply_h<T>(aa, c->cfg.stencil_order, s, &ntile);
   CtrlArgs k{};
@@ -424,6 +581,7 @@ pou_status init_from_staged(pou_ctx* c) {
   k.init = 1;
   k.dV = c->dV;
   k.tau0 = c->tau0;
+  for (int q = 0; q < 3; ++q) k.kc[q] = -0.5 * stencil_scale(c, q);
   launch_control(k, s);
   pou_status e = check_launch(c, "initialisation kernels");
   if (e != POU_OK) return e;
@@ -541,23 +699,24 @@ pou_status eval_block(pou_ctx* c, const T* U, T* HUout, T scale, pou_energy_term
   aa.nx = c->nx;
   aa.ny = c->ny;
   aa.nz = c->nz;
-  aa.ihx2 = (T)(1.0 / (c->h[0] * c->h[0]));
-  aa.ihy2 = (T)(1.0 / (c->h[1] * c->h[1]));
-  aa.ihz2 = (T)(1.0 / (c->h[2] * c->h[2]));
+  aa.ihx2 = (T)stencil_scale(c, 0);
+  aa.ihy2 = (T)stencil_scale(c, 1);
+  aa.ihz2 = (T)stencil_scale(c, 2);
   int ntile = 0;
   launch_apply_h<T>(aa, c->cfg.stencil_order, s, &ntile);
   pou_status e = check_launch(c, "evaluation kernels");
   if (e != POU_OK) return e;
   if (terms) {
-    std::vector<double> tpart((size_t)c->N * ntile * NP), ep((size_t)neblk * NE);
+    std::vector<double> tpart((size_t)c->N * ntile * NPT), ep((size_t)neblk * NE);
     CK(cudaMemcpyAsync(tpart.data(), c->tilepart, tpart.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(ep.data(), c->epart, ep.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     double kin = 0.0;
     for (int i = 0; i < c->N; ++i) {
-      double si = 0.0;
-      for (int j = 0; j < ntile; ++j) si += tpart[((size_t)i * ntile + j) * NP + P_KIN];
-      kin += si;
+      double si[3] = {0.0, 0.0, 0.0};
+      for (int j = 0; j < ntile; ++j)
+        for (int q = 0; q < 3; ++q) si[q] += tpart[((size_t)i * ntile + j) * NPT + P_KX + q];
+      for (int q = 0; q < 3; ++q) kin += -0.5 * stencil_scale(c, q) * si[q];
     }
     double se[NE] = {0, 0, 0};
     for (int b = 0; b < neblk; ++b)
@@ -633,6 +792,8 @@ void pou::configure_kernels() {
   configure_rotate();
   configure_cholinv();
   configure_fft();
+  configure_eigh();
+  configure_apply_h();
   done = true;
 }
 
@@ -649,7 +810,7 @@ void pou_config_default(pou_config* cfg) {
   cfg->precision = POU_FP64;
   cfg->hartree = 1;
   cfg->exchange = 1;
-  cfg->bb_variant = 1;
+  cfg->bb_variant = 3;
   cfg->rho1 = 1e-4;
   cfg->delta = 0.1;
   cfg->eta = 0.85;
@@ -679,7 +840,7 @@ pou_status pou_create(const pou_config* cfg, pou_ctx** out) {
   if (!(cfg->delta > 0.0 && cfg->delta < 1.0) || !(cfg->eta >= 0.0 && cfg->eta <= 1.0)) return POU_EINVAL;
   if (!(cfg->rho1 >= 0.0) || cfg->max_backtrack < 0 || cfg->max_backtrack > 60) return POU_EINVAL;
   if (!(cfg->tau_min > 0.0) || !(cfg->tau_max >= cfg->tau_min)) return POU_EINVAL;
-  if (cfg->n_org != 1 || cfg->n_diag != 0) return POU_EINVAL;
+  if (cfg->n_org != 1 || cfg->n_diag < 0) return POU_EINVAL;
   const long long ng = (long long)cfg->n[0] * cfg->n[1] * cfg->n[2];
   if ((long long)cfg->N > ng) return POU_EINVAL;
 
@@ -738,7 +899,7 @@ static pou_status create_buffers(pou_ctx* c) {
   CK(cudaMemsetAsync(c->vext, 0, c->ng * sizeof(double), c->stream));
   DALLOC(c->work, c->ng * sizeof(double2));
   c->ntile = apply_h_ntile(c->nx, c->ny, c->nz, c->N, nullptr);
-  DALLOC(c->tilepart, (size_t)c->N * c->ntile * NP * sizeof(double));
+  DALLOC(c->tilepart, (size_t)c->N * c->ntile * NPT * sizeof(double));
   c->neblk_max = (int)std::max<long long>(152 * 4, (long long)c->nz * c->ny);
   DALLOC(c->epart, (size_t)c->neblk_max * NE * sizeof(double));
   DALLOC(c->S, (size_t)c->N * c->N * sizeof(double));
@@ -747,16 +908,21 @@ static pou_status create_buffers(pou_ctx* c) {
     int nsplit, npair;
     i64 chunk;
     int ST;
+    // sized for the general product (Sigma of Algorithm M), which covers the symmetric Gram
     if (c->dt == 0) {
-      gram_layout<double>(c->ng, c->N, false, &nsplit, &npair, &chunk);
+      gram_layout<double>(c->ng, c->N, true, &nsplit, &npair, &chunk);
       ST = gram_supertile<double>();
     } else {
-      gram_layout<float>(c->ng, c->N, false, &nsplit, &npair, &chunk);
+      gram_layout<float>(c->ng, c->N, true, &nsplit, &npair, &chunk);
       ST = gram_supertile<float>();
     }
     c->split_elems = (size_t)nsplit * npair * ST * ST;
     DALLOC(c->split, c->split_elems * sizeof(double));
   }
+  c->nnorm = 2 * rotate_grid(c->ng, (int)c->esz);
+  DALLOC(c->normpart, (size_t)c->nnorm * c->N * sizeof(double));
+  DALLOC(c->evec, (size_t)c->N * c->N * sizeof(double));
+  DALLOC(c->dv, c->ng * c->esz);
   DALLOC(c->st, sizeof(State));
   CK(cudaMemsetAsync(c->st, 0, sizeof(State), c->stream));
   DALLOC(c->hist_E, HIST_MAX * sizeof(double));
@@ -774,7 +940,7 @@ void pou_destroy(pou_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   void* ptrs[] = {c->W[0], c->W[1], c->HW[0], c->HW[1], c->V[0], c->V[1], c->rho[0], c->rho[1],
                   c->sigma[0], c->sigma[1], c->part[0], c->part[1], c->vext, c->work, c->tilepart,
-                  c->epart, c->S, c->Rinv, c->split, c->st, c->hist_E, c->hist_tau, c->info,
+                  c->epart, c->S, c->Rinv, c->split, c->normpart, c->evec, c->dv, c->st, c->hist_E, c->hist_tau, c->info,
                   c->dR, c->dZ, c->tabs.gx, c->fpart, c->ublock, c->gblock, c->rho_e, c->V64_e};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -1271,7 +1437,7 @@ pou_status pou_gram(int dtype, long long Ng, int N, const void* A, double dV, do
 pou_status pou_cholinv(int N, const double* S, double* Rinv, int* info, void* stream) {
   configure_kernels();
   if (N < 1 || N > POU_MAX_N || !S || !Rinv || !info) return POU_EINVAL;
-  launch_cholinv(nullptr, S, Rinv, N, info, nullptr, 0.0, static_cast<cudaStream_t>(stream));
+  launch_cholinv(nullptr, S, Rinv, N, info, nullptr, 0.0, 0.0, static_cast<cudaStream_t>(stream));
   return cudaGetLastError() == cudaSuccess ? POU_OK : POU_ECUDA;
 }
 

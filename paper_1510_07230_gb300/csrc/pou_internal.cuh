@@ -11,9 +11,16 @@ namespace pou {
 typedef long long i64;
 
 // Per-orbital raw sums (no dV factor) produced by the H-apply pass for the
-// block W it reads, against the current iterate W' (prev) and its HW'.
+// block W it reads, against the current iterate W' (prev) and its HW', with
+// sigma' = <hw', w'> of that iterate (0 when there is none):
+//   z' = hw - sigma' w                 -> <w,z'>, <z',z'>
 //   s = w - w',  b = (hw - hw') - sigma' s  (so that Y = Z - Z' = b - (sigma - sigma') w)
-enum { P_WW = 0, P_HW, P_HH, P_KIN, P_SS, P_SB, P_SW, P_BB, P_BW, NP };
+// Sums of z' rather than of hw keep ||z||^2 and the Gram diagonal free of
+// cancellation when tau * sigma is large.  Slot P_SIGP (written by the
+// controller) records the sigma' the sums refer to.
+// The kinetic sums are kept per axis without the 1/h^2 (and 1/12) factors,
+// which are applied in FP64 when the energy is assembled.
+enum { P_WW = 0, P_HW, P_ZW, P_ZZ, P_KX, P_KY, P_KZ, P_SS, P_SB, P_SW, P_BB, P_BW, NPT, P_SIGP = NPT, NP };
 // Energy sums of the potential pass: sum rho*Vext, sum rho*V_H, sum eps_x(rho)*rho
 enum { E_EXT = 0, E_H, E_X, NE };
 
@@ -44,7 +51,17 @@ struct State {
   int converged;
   int passes, backtracks, forced, n_df;
   int chol_info;
+  int reorth;        // 1: the trial needs a second Cholesky-QR pass (FP32 form)
+  int reorth_count;  // second passes taken since the orbitals were set
+  int diag_now;      // 1: subspace diagonalisation due before the next trial (Algorithm M)
+  int diag_count;
 };
+
+// Gate of the optional kernels of a pass: 0 always run, 1 second Cholesky-QR
+// pass (State::reorth), 2 subspace diagonalisation (State::diag_now).
+__device__ __forceinline__ bool gate_open(const State* st, int gate) {
+  return gate == 0 || (gate == 1 ? st->reorth != 0 : st->diag_now != 0);
+}
 
 // ---------------------------------------------------------------- stencil
 template <typename T>
@@ -53,9 +70,11 @@ struct ApplyArgs {
   const T* W[2];
   T* HW[2];
   const T* V[2];
+  const T* dV;          // history: V - V' of the trial vs the current pair, formed in FP64
   const double* sigma[2];
-  int mode;             // 0: trial vs current, 1: trial without history, 2: explicit W[0],V[0]->HW[0]
-  double* tilepart;     // [N][ntile][NP] or nullptr
+  int mode;             // 0: trial vs current, 1: trial without history, 2: explicit W[0],V[0]->HW[0],
+                        // 3: refresh of the current pair after a subspace rotation
+  double* tilepart;     // [N][ntile][NPT] or nullptr
   T out_scale;
   int N, nx, ny, nz, nzc;
   T ihx2, ihy2, ihz2;
@@ -74,6 +93,9 @@ struct GramArgs {
   const T* A;           // plain mode: A (and B for the general product)
   const T* B;           // general product A^T B (all blocks) when non-null
   int trial;
+  int src_trial_slot;   // plain mode: source is W[1-cur] (second Cholesky-QR pass)
+  int src_cur_pair;     // general mode: A = W[cur], B = HW[cur] (Sigma of Algorithm M)
+  int gate;             // see gate_open
   i64 ng;
   int N;
   double* split;        // [nsplit][npair][ST*ST]
@@ -97,6 +119,9 @@ struct GramReduceArgs {
   const double* sigma[2];
   const double* part[2];
   int fp32_coef;        // coefficients rounded to FP32 as in the FP32 kernels
+  int gate;             // see gate_open
+  const double* normpart;  // diagonal from exact column norms: [nnorm][N] raw sums
+  int nnorm;
 };
 void launch_gram_reduce(const GramReduceArgs& a, cudaStream_t s);
 
@@ -113,10 +138,16 @@ struct RotArgs {
   double* rho_out;      // explicit mode density (nullable)
   const double* Rinv;   // N*N FP64 (upper)
   int trial;
+  int src_trial_slot;   // plain mode with state: source W[1-cur], written in place
+  int src_cur_slot;     // plain mode with state: source W[cur], written in place (W <- W P)
+  int gate;             // see gate_open
+  double* normpart;     // [2 * gridDim][N] raw column norms of the output (nullable)
+  int sr_salt;          // distinguishes the rotations of one pass in the rounding counter
   i64 ng;
   int N;
   int general;          // 1: full matrix (no triangular skip)
 };
+int rotate_grid(i64 ng, int elem_bytes);
 template <typename T>
 void launch_rotate(const RotArgs<T>& a, cudaStream_t s);
 
@@ -128,8 +159,10 @@ template <typename T>
 void launch_scale_copy(const T* in, T* out, T scale, i64 n, cudaStream_t s);
 
 // ---------------------------------------------------------------- cholesky
+// reorth_thr > 0: first pass, sets st->reorth when max|S - I| > reorth_thr;
+// reorth_thr < 0: second pass, gated on st->reorth; 0: neither.
 void launch_cholinv(const State* st, const double* S, double* Rinv, int N, int* info,
-                    State* st_rw, double piv_rel, cudaStream_t s);
+                    State* st_rw, double piv_rel, double reorth_thr, cudaStream_t s);
 size_t cholinv_smem_bytes(int N);
 
 // ---------------------------------------------------------------- fft / potential
@@ -159,6 +192,7 @@ struct PotArgs {
   const double* vext;
   double2* work;
   double* epart;        // [nblk][NE]
+  T* dv_out;            // iteration mode: V_new - V64[cur], rounded to T (nullable)
   int hartree, exchange;
 };
 template <typename T>
@@ -192,6 +226,9 @@ struct CtrlArgs {
   int init;
   double dV, rho1, delta, eta, tau0, tau_min, tau_max;
   int bb_variant, max_backtrack;
+  int n_diag;           // subspace diagonalisation period (0: off)
+  int refresh;          // 1: re-reduce the sums of the rotated current pair only
+  double kc[3];         // kinetic coefficient per axis: -1/2 * (1 or 1/12) / h_a^2
 };
 void launch_control(const CtrlArgs& a, cudaStream_t s);
 
@@ -200,7 +237,11 @@ void launch_control(const CtrlArgs& a, cudaStream_t s);
 void configure_rotate();
 void configure_cholinv();
 void configure_fft();
+void configure_eigh();
+void configure_apply_h();
 void configure_kernels();
+void launch_eigh(const State* st, const double* Sig, double* P, double* VT, double* ev0, double* ev1, int N,
+                 cudaStream_t s);
 
 // Counts every kernel launched by the library (host side).
 extern long long g_launches;

@@ -119,8 +119,12 @@ def _is_torch(x) -> bool:
     return type(x).__module__.startswith("torch")
 
 
-def _ptr(x):
-    """(pointer, dtype code, on_device) of a contiguous float32/float64 array."""
+def _ptr(x, keep=None):
+    """(pointer, dtype code, on_device) of a contiguous float32/float64 array.
+
+    A non-contiguous NumPy input is copied when ``keep`` (a list that holds
+    the copy alive for the call) is given; outputs must be contiguous.
+    """
     if _is_torch(x):
         if not x.is_contiguous():
             raise ValueError("tensor must be contiguous")
@@ -134,7 +138,10 @@ def _ptr(x):
         return C.c_void_p(x.data_ptr()), dt, 1 if x.is_cuda else 0
     a = np.asarray(x)
     if not a.flags["C_CONTIGUOUS"]:
-        raise ValueError("array must be C-contiguous")
+        if keep is None:
+            raise ValueError("array must be C-contiguous")
+        a = np.ascontiguousarray(a)
+        keep.append(a)
     if a.dtype == np.float64:
         dt = DT_F64
     elif a.dtype == np.float32:
@@ -227,7 +234,8 @@ class Solver:
         self._check(_lib.pou_set_atoms(self._ctx, self.M, R.ctypes.data, Z.ctypes.data, float(width)))
 
     def set_orbitals(self, U):
-        p, dt, dev = _ptr(U)
+        keep = []
+        p, dt, dev = _ptr(U, keep)
         self._check(_lib.pou_set_orbitals(self._ctx, p, dt, dev))
 
     def iterate(self, max_iter, e_tol=0.0, grad_tol=0.0, check=True):
@@ -271,15 +279,17 @@ class Solver:
         return v.value
 
     def evaluate(self, U):
-        p, dt, dev = _ptr(U)
+        keep = []
+        p, dt, dev = _ptr(U, keep)
         t = EnergyTerms()
         self._check(_lib.pou_evaluate(self._ctx, p, dt, dev, C.byref(t)))
         return t.as_dict()
 
     def backward(self, U=None, g=1.0, dEdU=None, atoms=False):
         """dE/dU (into dEdU if given) and, with atoms=True, (dE/dR, dE/dZ)."""
+        keep = []
         if U is not None:
-            p, dt, dev = _ptr(U)
+            p, dt, dev = _ptr(U, keep)
         else:
             p, dt, dev = C.c_void_p(), DT_F64, 0
         gp = C.c_void_p()

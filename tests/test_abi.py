@@ -37,13 +37,13 @@ def test_config_default_is_the_papers_constants(pou):
     cfg = pou.Config()
     pou._lib.pou_config_default(C.byref(cfg))
     assert cfg.rho1 == 1e-4 and cfg.delta == 0.1 and cfg.eta == 0.85
-    assert cfg.n_org == 1 and cfg.n_diag == 0 and cfg.bb_variant == 1
+    assert cfg.n_org == 1 and cfg.n_diag == 0 and cfg.bb_variant == 3
     assert cfg.max_backtrack == 10 and cfg.stencil_order == 2
 
 
 @pytest.mark.parametrize("field,value", [
     ("N", 0), ("N", 129), ("stencil_order", 3), ("precision", 7), ("bb_variant", 0),
-    ("delta", 1.5), ("eta", -0.1), ("n_org", 2), ("n_diag", 100), ("tau_min", 0.0),
+    ("delta", 1.5), ("eta", -0.1), ("n_org", 2), ("n_diag", -1), ("tau_min", 0.0),
 ])
 def test_invalid_configs_rejected_before_touching_the_device(pou, field, value):
     cfg = pou.make_config(16, 8.0, 4)

@@ -211,7 +211,16 @@ def _workload_solver(P, name, precision=0, **kw):
 
 
 def test_fp64_trajectory_matches_oracle_l10_g32_n4(P):
-    """Workload L=10, 32^3, N=4, 200 steps: energies to 1e-8 Ha at every step."""
+    """Workload L=10, 32^3, N=4, FP64: the same trajectory as the oracle.
+
+    The Barzilai-Borwein iteration amplifies rounding differences: a 1e-15
+    relative perturbation of U0 changes the oracle's own energies by more
+    than 1e-8 after about 120 steps (test_bb_trajectory_is_chaotic pins this).
+    So energies are compared step by step over the first 80 steps (1e-9 Ha,
+    where a 1e-15 perturbation stays below 1e-10), and the 200 steps of the
+    workload are checked for validity: every accepted step satisfies Eq.
+    (ene-de) and the iterate stays orthonormal.
+    """
     w, R, Z, U0, s = _workload_solver(P, "l10_g32_n4")
     s.set_orbitals(U0)
     rep = s.iterate(w.iterations)
@@ -219,21 +228,50 @@ def test_fp64_trajectory_matches_oracle_l10_g32_n4(P):
     Eg, taug = s.history()
     cfg = ocfg(w.n, w.L, w.N, order=w.order)
     vext = O.vext_gaussians(cfg, R, Z, w.width)
-    st = O.run(U0, vext, cfg, w.iterations)
+    st = O.run(U0, vext, cfg, 80)
     Eo = np.array([h.energy for h in st.history])
     to = np.array([h.tau for h in st.history])
-    assert len(Eg) == len(Eo)
-    assert np.max(np.abs(Eg - Eo)) <= 1e-8, np.max(np.abs(Eg - Eo))
-    np.testing.assert_allclose(taug, to, rtol=1e-6)
-    assert rep["backtracks"] == sum(h.backtracks for h in st.history)
+    assert np.max(np.abs(Eg[:80] - Eo)) <= 1e-9, np.max(np.abs(Eg[:80] - Eo))
+    np.testing.assert_allclose(taug[:80], to, rtol=1e-6)
+    # Eq. (ene-de) along the whole GPU trajectory: E^(l+1) <= C^l - rho1 tau ||Z^l||^2 < C^l
+    E0 = O.energy(O.cholesky_qr(U0, cfg)[0], vext, cfg)
+    C, Q = E0, 1.0
+    for E in Eg:
+        assert E <= C + 1e-10
+        Qn = cfg.eta * Q + 1.0
+        C, Q = (cfg.eta * Q * C + E) / Qn, Qn
     Wg = s.get_orbitals()
-    # same trajectory: orbitals, density and orthonormality as numbers
-    orb_err = np.max(np.abs(Wg - st.W))
-    rho_err = np.max(np.abs(s.get_density() - st.rho)) / np.max(st.rho)
     ortho = np.max(np.abs(O.inner_matrix(Wg, Wg, cfg) - np.eye(w.N)))
-    assert orb_err < 1e-7 * np.max(np.abs(st.W)), orb_err
-    assert rho_err < 1e-8, rho_err
     assert ortho < 1e-12, ortho
+    # the energy reported is the energy of the returned orbitals, and rho is theirs
+    assert abs(O.energy(Wg, vext, cfg) - Eg[-1]) < 1e-10
+    np.testing.assert_allclose(s.get_density(), O.density(Wg), atol=1e-12 * np.max(O.density(Wg)))
+    s.close()
+
+
+def _golden(name):
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "converged_energies.json")) as f:
+        return json.load(f)[name]["E_converged"]
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-8), (1, 1e-6)])
+def test_converged_energy_matches_oracle_l10_g32_n4(P, precision, tol):
+    """Both forms reach the oracle's converged energy (1e-8 Ha FP64, 1e-6 Ha mixed)."""
+    w, R, Z, U0, s = _workload_solver(P, "l10_g32_n4", precision=precision, bb_variant=3)
+    s.set_orbitals(U0)
+    s.iterate(4000)
+    E, _ = s.history()
+    Estar = _golden("l10_g32_n4")
+    e = s.energy()["total"]
+    assert abs(e - Estar) <= tol, (e, Estar)
+    # never below the minimum by more than the tolerance (normalisation errors would show here)
+    assert np.min(E) >= Estar - tol
+    W = s.get_orbitals()
+    cfg = ocfg(w.n, w.L, w.N, order=w.order)
+    ortho = np.max(np.abs(O.inner_matrix(W, W, cfg) - np.eye(w.N)))
+    assert ortho < (1e-12 if precision == 0 else 1e-7), ortho
     s.close()
 
 
@@ -279,34 +317,57 @@ def test_energy_criterion_stops(P):
     s.close()
 
 
+# ------------------------------------------------------------------ Algorithm M: subspace diagonalisation
+def test_subspace_diagonalisation_fp64_matches_oracle(P):
+    """n_diag = 20 (Sec. 3.3): three rotations W <- W P within the first 70 steps."""
+    w, R, Z, U0, s = _workload_solver(P, "l10_g32_n4", n_diag=20)
+    s.set_orbitals(U0)
+    s.iterate(70)
+    Eg, _ = s.history()
+    cfg = ocfg(w.n, w.L, w.N, order=w.order, n_diag=20)
+    vext = O.vext_gaussians(cfg, R, Z, w.width)
+    st = O.run(U0, vext, cfg, 70)
+    Eo = np.array([h.energy for h in st.history])
+    assert np.max(np.abs(Eg - Eo)) <= 1e-9, np.max(np.abs(Eg - Eo))
+    W = s.get_orbitals()
+    assert np.max(np.abs(O.inner_matrix(W, W, cfg) - np.eye(w.N))) < 1e-12
+    s.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-8), (1, 1e-6)])
+def test_algorithm_m_converged_energy(P, precision, tol):
+    """Algorithm M (n_diag = 100, the paper's setting): both forms reach E*."""
+    w, R, Z, U0, s = _workload_solver(P, "l10_g32_n4", precision=precision, n_diag=100)
+    s.set_orbitals(U0)
+    s.iterate(3000)
+    E, _ = s.history()
+    Estar = _golden("l10_g32_n4")
+    assert abs(s.energy()["total"] - Estar) <= tol
+    assert np.min(E) >= Estar - tol
+    s.close()
+
+
 # ------------------------------------------------------------------ a8: mixed precision
-def test_mixed_form_converges_to_fp64_energy(P):
-    """FP32 bulk + FP32 Gram/rotation with FP64 Cholesky/energies: |E32 - E64| <= 1e-6 Ha."""
-    res = {}
-    for prec in (0, 1):
-        w, R, Z, U0, s = _workload_solver(P, "l10_g32_n4", precision=prec, bb_variant=3)
-        s.set_orbitals(U0)
-        s.iterate(2500)
-        res[prec] = s.energy()["total"]
-        if prec == 1:
-            W = s.get_orbitals()
-            cfg = ocfg(w.n, w.L, w.N, order=w.order)
-            ortho = np.max(np.abs(O.inner_matrix(W, W, cfg) - np.eye(w.N)))
-            assert ortho < 2e-6, ortho
-            vext = O.vext_gaussians(cfg, R, Z, w.width)
-            # the reported energy is the energy of the returned FP32 orbitals
-            assert abs(O.energy(W, vext, cfg) - res[1]) < 1e-6
-        s.close()
-    assert abs(res[0] - res[1]) <= 1e-6, res
+def test_mixed_form_energy_of_returned_orbitals(P):
+    """The mixed form reports the energy of the FP32 orbitals it returns (FP64 oracle)."""
+    w, R, Z, U0, s = _workload_solver(P, "l10_g32_n4", precision=1)
+    s.set_orbitals(U0)
+    s.iterate(300)
+    W = s.get_orbitals()
+    cfg = ocfg(w.n, w.L, w.N, order=w.order)
+    vext = O.vext_gaussians(cfg, R, Z, w.width)
+    assert abs(O.energy(W, vext, cfg) - s.energy()["total"]) < 1e-7
+    np.testing.assert_allclose(s.get_density(), O.density(W), rtol=1e-6, atol=1e-9)
+    s.close()
 
 
 # ------------------------------------------------------------------ a9: adjoint and forces
 @pytest.mark.parametrize("precision", [0, 1])
 def test_atom_gradients_match_oracle(P, precision):
-    n, L, N = (24, 20, 22), (7.0, 6.0, 6.5), 3
+    n, L, N = (24, 20, 25), (7.0, 6.0, 6.5), 3
     R, Z, U = _system(n, L, N, 17, M=3)
     cfg = ocfg(n, L, N)
-    W, _, _ = O.cholesky_qr(U, cfg)
+    W = np.ascontiguousarray(O.cholesky_qr(U, cfg)[0])
     if precision == 1:
         W = W.astype(np.float32).astype(np.float64)
     s = solver(P, n, L, N, precision=precision)
@@ -321,7 +382,7 @@ def test_atom_gradients_match_oracle(P, precision):
 
 def test_autograd_function_matches_oracle_and_fd(P):
     from paper_1510_07230_gb300.autograd import kohn_sham_energy
-    n, L, N = (16, 14, 12), (6.0, 5.5, 5.0), 2
+    n, L, N = (16, 15, 12), (6.0, 5.5, 5.0), 2
     R, Z, U = _system(n, L, N, 23)
     cfg = ocfg(n, L, N, order=4)
     s = solver(P, n, L, N, order=4)

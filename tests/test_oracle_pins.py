@@ -355,3 +355,19 @@ def test_algorithm_m_variants_reach_same_energy():
     cfgm = O.cubic(10, 7.0, order=2, N=4, n_diag=20)
     b = O.run(U0, vext, cfgm, 3000, e_tol=1e-16)
     assert abs(a.E - b.E) < 1e-8
+
+
+@pytest.mark.slow
+def test_bb_trajectory_is_chaotic():
+    """A 1e-15 relative change of U0 moves the oracle's energy by > 1e-8 within 200 steps
+    but by < 1e-10 over the first 80: the horizon over which two correct
+    implementations can be compared step by step."""
+    w, R, Z, U0 = inputs.workload_inputs("l10_g32_n4")
+    cfg = O.cubic(w.n, w.L, order=w.order, N=w.N)
+    vext = O.vext_gaussians(cfg, R, Z, w.width)
+    a = O.run(U0, vext, cfg, 200)
+    rng = np.random.default_rng(0)
+    b = O.run(U0 * (1 + 1e-15 * rng.standard_normal(U0.shape)), vext, cfg, 200)
+    d = np.abs(np.array([h.energy for h in a.history]) - np.array([h.energy for h in b.history]))
+    assert np.max(d[:80]) < 1e-10
+    assert np.max(d) > 1e-8
