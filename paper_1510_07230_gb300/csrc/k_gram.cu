@@ -51,33 +51,25 @@ __device__ __forceinline__ void add_square(F2& a, float x) {
 }
 __device__ __forceinline__ void add_f2(F2& a, const F2& b) { two_sum_add(a, b.s, b.c); }
 
-// SplitMix64 output function (Steele, Lea and Flood, 2014), used as a
-// counter-based source of uniform bits.
-__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
-  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
-  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
-  return z ^ (z >> 31);
+// 32-bit integer mixer "lowbias32" (C. Wellons, hash-prospector), used as a
+// counter-based source of uniform bits for the dithered rounding below.
+__device__ __forceinline__ unsigned mix32(unsigned x) {
+  x ^= x >> 16;
+  x *= 0x7feb352dU;
+  x ^= x >> 15;
+  x *= 0x846ca68bU;
+  x ^= x >> 16;
+  return x;
 }
 
-// t + r rounded to FP32 without bias: with d the exact residual of the
-// nearest rounding s, the neighbour on d's side is chosen with probability
-// |d| / ulp, so the expected stored value is t + r.  Near convergence the
-// corrections that keep an orbital normalised are below half an ulp of every
-// element, and round-to-nearest would drop them all the same way.
-__device__ __forceinline__ float round_unbiased(float t, float r, unsigned long long key) {
-  const float s = t + r;
-  const float d = (t - s) + r;  // exact when |t| >= |r|
-  if (d == 0.f) return s;
-  const float nb = nextafterf(s, d > 0.f ? INFINITY : -INFINITY);
-  const float prob = d / (nb - s);
-  const float u = (float)(mix64(key) >> 40) * (1.0f / 16777216.0f);
-  return u < prob ? nb : s;
-}
-
-template <typename T>
-__device__ __forceinline__ T trial_value(const T* W, const T* H, T coef, T tau, i64 off) {
-  // (1 + tau sigma) w - tau hw
-  return coef * W[off] - tau * H[off];
+// Unbiased rounding: fma(a, x, rest + d) with d uniform in (-ulp/2, ulp/2)
+// of the result rounds a x + rest up or down with probabilities that make
+// the expected stored value exact.  Near convergence the corrections that
+// keep an orbital normalised are below half an ulp of every element, and
+// plain round-to-nearest would drop them all the same way.
+__device__ __forceinline__ float dither(float x, unsigned byte) {
+  const float ulp = __uint_as_float(__float_as_uint(x) & 0x7f800000u) * 1.1920928955078125e-7f;
+  return ((float)byte * (1.0f / 256.0f) - 0.498046875f) * ulp;
 }
 
 // Gram of a block over the grid dimension.  Work unit: a tile of BK
@@ -359,8 +351,8 @@ __global__ void __launch_bounds__(RNT) k_rotate(RotArgs<T> a, int nchunks) {
   }
   __syncthreads();
   // counter for the unbiased rounding: one stream per pass and per use
-  const unsigned long long seed =
-      ((unsigned long long)(a.st ? a.st->passes : 0) << 2 | (unsigned long long)a.sr_salt) * 0x9e3779b97f4a7c15ULL;
+  const unsigned seed32 = mix32((unsigned)(a.st ? a.st->passes : 0) * 4u + (unsigned)a.sr_salt + 0x85ebca6bu);
+  const bool vec4 = (a.ng % 4) == 0;  // 16-byte aligned rows of four points
 
   const int lane = tid & 31, warp = tid >> 5;
   const int jw = warp & 3, pw = warp >> 2;
@@ -376,15 +368,33 @@ __global__ void __launch_bounds__(RNT) k_rotate(RotArgs<T> a, int nchunks) {
 
   for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const i64 p0 = (i64)ch * RP;
-    for (int idx = tid; idx < N * RP; idx += RNT) {
-      const int i = idx / RP, pp = idx % RP;
-      const i64 gp = p0 + pp;
-      T v = T(0);
-      if (gp < ng) {
-        const i64 off = (i64)i * ng + gp;
-        v = a.trial ? coefs[i] * Wsrc[off] - tauT * Hsrc[off] : Wsrc[off];
+    if (sizeof(T) == 4 && vec4 && p0 + RP <= ng) {
+      // four points per load
+      for (int idx = tid; idx < N * (RP / 4); idx += RNT) {
+        const int i = idx / (RP / 4), pp = 4 * (idx % (RP / 4));
+        const i64 off = (i64)i * ng + p0 + pp;
+        float4 v = *reinterpret_cast<const float4*>(&Wsrc[off]);
+        if (a.trial) {
+          const float4 h = *reinterpret_cast<const float4*>(&Hsrc[off]);
+          const float cf = (float)coefs[i], tf = (float)tauT;
+          v.x = cf * v.x - tf * h.x;
+          v.y = cf * v.y - tf * h.y;
+          v.z = cf * v.z - tf * h.z;
+          v.w = cf * v.w - tf * h.w;
+        }
+        *reinterpret_cast<float4*>(&Xs[i * XS + pp]) = v;
       }
-      Xs[i * XS + pp] = v;
+    } else {
+      for (int idx = tid; idx < N * RP; idx += RNT) {
+        const int i = idx / RP, pp = idx % RP;
+        const i64 gp = p0 + pp;
+        T v = T(0);
+        if (gp < ng) {
+          const i64 off = (i64)i * ng + gp;
+          v = a.trial ? coefs[i] * Wsrc[off] - tauT * Hsrc[off] : Wsrc[off];
+        }
+        Xs[i * XS + pp] = v;
+      }
     }
     __syncthreads();
 
@@ -420,29 +430,32 @@ __global__ void __launch_bounds__(RNT) k_rotate(RotArgs<T> a, int nchunks) {
         const int j = j0 + jj;
         if (j >= N) continue;
         const float ah = self[j], al = self[NPAD + j], bh = self[2 * NPAD + j], bl = self[3 * NPAD + j];
+        const unsigned bits = mix32(seed32 ^ mix32((unsigned)j * 0x9e3779b1u ^ (unsigned)(p0 + pl0)));
+        float wv[4] = {0.f, 0.f, 0.f, 0.f}, hv[4] = {0.f, 0.f, 0.f, 0.f};
+        const i64 g0 = p0 + pl0;
+        if (a.trial) {
+          if (vec4 && g0 + 3 < ng) {
+            const float4 w4 = *reinterpret_cast<const float4*>(&Wsrc[(i64)j * ng + g0]);
+            const float4 h4 = *reinterpret_cast<const float4*>(&Hsrc[(i64)j * ng + g0]);
+            wv[0] = w4.x; wv[1] = w4.y; wv[2] = w4.z; wv[3] = w4.w;
+            hv[0] = h4.x; hv[1] = h4.y; hv[2] = h4.z; hv[3] = h4.w;
+          } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (g0 + q < ng) {
+                wv[q] = (float)Wsrc[(i64)j * ng + g0 + q];
+                hv[q] = (float)Hsrc[(i64)j * ng + g0 + q];
+              }
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) wv[q] = (float)Xs[j * XS + pl0 + q];
+        }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const i64 gp = p0 + pl0 + q;
-          float wv = 0.f, hv = 0.f;
-          if (gp < ng) {
-            if (a.trial) {
-              wv = (float)Wsrc[(i64)j * ng + gp];
-              hv = (float)Hsrc[(i64)j * ng + gp];
-            } else {
-              wv = (float)Xs[j * XS + pl0 + q];
-            }
-          }
-          const float off = (float)acc[jj][q];
-          const float p1 = wv * ah, e1 = fmaf(wv, ah, -p1);
-          const float p2 = hv * bh, e2 = fmaf(hv, bh, -p2);
-          const float t = p1 - p2;
-          const float bp = t - p1;
-          const float et = (p1 - (t - bp)) + (-p2 - bp);
-          const float u = t + off;
-          const float bq = u - t;
-          const float eu = (t - (u - bq)) + (off - bq);
-          const float r = ((e1 - e2) + (et + eu)) + (wv * al - hv * bl);
-          acc[jj][q] = (T)round_unbiased(u, r, seed ^ (unsigned long long)((i64)j * ng + gp));
+          const float d = dither(wv[q], (bits >> (8 * q)) & 0xffu);
+          const float rest = fmaf(al, wv[q], fmaf(-bl, hv[q], (float)acc[jj][q] + d));
+          acc[jj][q] = (T)fmaf(ah, wv[q], fmaf(-bh, hv[q], rest));
         }
       }
     }
