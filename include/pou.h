@@ -230,6 +230,28 @@ size_t pou_gram_workspace_bytes(int dtype, long long Ng, int N);
 pou_status pou_gram(int dtype, long long Ng, int N, const void* A, double dV, double* S,
                     void* workspace, size_t workspace_bytes, void* stream);
 
+/* Allocation-free Gram matrix: the result of pou_gram (same arguments
+ * without the workspace), for callers that cannot allocate device memory,
+ * for example code that runs while a stream is captured into a CUDA graph
+ * (cudaMalloc is not a stream operation and synchronises the device), loops
+ * that must not allocate after start-up, or hosts that give this library a
+ * fixed memory budget.  The paper has no counterpart: this is a library
+ * service, not a step of the method.
+ *  - The per-split partial sums live in one fixed buffer of static device
+ *    memory of POU_GRAM_NOALLOC_MAX_BYTES, which every GPU that loads the
+ *    library holds until the process exits; the call allocates nothing.
+ *  - The first call on a device looks up the buffer's device address, with
+ *    that device current; make that first call before any stream capture.
+ *  - The number of splits is capped to what fits the buffer, so results may
+ *    differ from pou_gram by rounding; N > POU_MAX_N (or a split that does
+ *    not fit) returns POU_EINVAL.
+ *  - Every call shares the buffer, and each call overwrites every part of
+ *    it that it reads, so nothing has to start at zero; calls that overlap
+ *    on the GPU (other streams, other host threads) race on the buffer and
+ *    must be serialised by the caller. */
+#define POU_GRAM_NOALLOC_MAX_BYTES (8u << 20)
+pou_status pou_gram_noalloc(int dtype, long long Ng, int N, const void* A, double dV, double* S, void* stream);
+
 /* Cholesky factor and triangular inverse (Sec. 3.2): S = R^T R with R upper
  * triangular and positive diagonal, Rinv = R^-1 (N*N device doubles,
  * row-major, lower part zero).  *info (device int) is 0 on success or k+1 if

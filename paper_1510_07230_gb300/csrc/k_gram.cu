@@ -615,6 +615,20 @@ void launch_gram(const GramArgs<T>& a, cudaStream_t s) {
 template void launch_gram<float>(const GramArgs<float>&, cudaStream_t);
 template void launch_gram<double>(const GramArgs<double>&, cudaStream_t);
 
+template <typename T>
+void launch_gram_nsplit(const GramArgs<T>& a, int nsplit, cudaStream_t s) {
+  int ns, npair;
+  i64 ntiles;
+  gram_layout<T>(a.ng, a.N, a.B != nullptr || a.src_cur_pair, &ns, &npair, &ntiles);
+  const int nsup = (a.N + GT<T>::ST - 1) / GT<T>::ST;
+  dim3 grid(nsplit, npair);
+  prof_begin("gram", s);
+  k_gram<T><<<grid, GNT, 0, s>>>(a, ntiles, nsup, npair);
+  prof_end(s);
+}
+template void launch_gram_nsplit<float>(const GramArgs<float>&, int, cudaStream_t);
+template void launch_gram_nsplit<double>(const GramArgs<double>&, int, cudaStream_t);
+
 void launch_gram_reduce(const GramReduceArgs& a, cudaStream_t s) {
   dim3 block(32, 8);
   dim3 grid((a.N + 31) / 32, (a.N + 7) / 8);

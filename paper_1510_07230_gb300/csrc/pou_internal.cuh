@@ -106,6 +106,10 @@ template <typename T>
 void gram_layout(i64 ng, int N, bool general, int* nsplit, int* npair, i64* chunk);
 template <typename T>
 void launch_gram(const GramArgs<T>& a, cudaStream_t s);
+// Same kernel with an explicit number of splits (each split writes one
+// npair * ST * ST block of FP64 partial sums).
+template <typename T>
+void launch_gram_nsplit(const GramArgs<T>& a, int nsplit, cudaStream_t s);
 
 struct GramReduceArgs {
   const State* st;

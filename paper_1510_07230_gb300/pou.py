@@ -92,6 +92,7 @@ _SIG = {
     "pou_get_profile": (_I, [_P, _I, _P, _P, _P, C.POINTER(C.c_int)]),
     "pou_gram_workspace_bytes": (C.c_size_t, [_I, C.c_longlong, _I]),
     "pou_gram": (_I, [_I, C.c_longlong, _I, _P, _D, _P, _P, C.c_size_t, _P]),
+    "pou_gram_noalloc": (_I, [_I, C.c_longlong, _I, _P, _D, _P, _P]),
     "pou_cholinv": (_I, [_I, _P, _P, _P, _P]),
     "pou_rotate": (_I, [_I, C.c_longlong, _I, _P, _P, _P, _P, _P]),
     "pou_hartree_workspace_bytes": (C.c_size_t, [C.POINTER(C.c_int)]),
@@ -358,6 +359,16 @@ def gram(A, dV, S, workspace, stream=None):
                        workspace.numel() * workspace.element_size(), _stream_ptr(stream))
     if st != OK:
         raise PouError(st, "pou_gram")
+
+
+def gram_noalloc(A, dV, S, stream=None):
+    """S = dV A^T A like gram(), with no workspace: the library's fixed device buffer."""
+    N = A.shape[0]
+    ng = A.numel() // N
+    p, dt, _ = _ptr(A)
+    st = _lib.pou_gram_noalloc(dt, ng, N, p, float(dV), C.c_void_p(S.data_ptr()), _stream_ptr(stream))
+    if st != OK:
+        raise PouError(st, "pou_gram_noalloc")
 
 
 def gram_workspace_bytes(dtype_code, ng, N):
