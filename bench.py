@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="l30_g160_n128")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--bb-variant", type=int, default=1)
+    ap.add_argument("--bb-variant", type=int, default=3)
     ap.add_argument("--force-every", type=int, default=10)
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")

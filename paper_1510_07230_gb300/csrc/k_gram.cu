@@ -239,7 +239,14 @@ __global__ void k_gram_reduce(GramReduceArgs a) {
   const i64 off = (i64)p * ST * ST + (r % ST) * ST + (c % ST);
   const i64 stride = (i64)a.npair * ST * ST;
   double s = 0.0;
-  for (int k = 0; k < a.nsplit; ++k) s += a.split[off + k * stride];
+  if (!a.general && I == J) {
+    // diagonal super-tile: symmetric part (the tensor-core kernel stores an
+    // unsymmetrised product; for the others both halves are equal)
+    const i64 offt = (i64)p * ST * ST + (c % ST) * ST + (r % ST);
+    for (int k = 0; k < a.nsplit; ++k) s += 0.5 * (a.split[off + k * stride] + a.split[offt + k * stride]);
+  } else {
+    for (int k = 0; k < a.nsplit; ++k) s += a.split[off + k * stride];
+  }
   s *= a.dV;
   if (a.trial && r == c) {
     // FP64 norm of the trial column a w - t hw (a, t: the coefficients as the
@@ -602,10 +609,25 @@ template void gram_layout<float>(i64, int, bool, int*, int*, i64*);
 template void gram_layout<double>(i64, int, bool, int*, int*, i64*);
 
 template <typename T>
+static bool use_tc(const GramArgs<T>& a) {
+  if constexpr (sizeof(T) == 4) {
+    return gram_tc_eligible(a);
+  } else {
+    return false;
+  }
+}
+
+template <typename T>
 void launch_gram(const GramArgs<T>& a, cudaStream_t s) {
   int nsplit, npair;
   i64 ntiles;
   gram_layout<T>(a.ng, a.N, a.B != nullptr || a.src_cur_pair, &nsplit, &npair, &ntiles);
+  if constexpr (sizeof(T) == 4) {
+    if (use_tc(a)) {
+      launch_gram_tc(a, nsplit, s);
+      return;
+    }
+  }
   const int nsup = (a.N + GT<T>::ST - 1) / GT<T>::ST;
   dim3 grid(nsplit, npair);
   prof_begin("gram", s);
@@ -620,6 +642,12 @@ void launch_gram_nsplit(const GramArgs<T>& a, int nsplit, cudaStream_t s) {
   int ns, npair;
   i64 ntiles;
   gram_layout<T>(a.ng, a.N, a.B != nullptr || a.src_cur_pair, &ns, &npair, &ntiles);
+  if constexpr (sizeof(T) == 4) {
+    if (use_tc(a)) {
+      launch_gram_tc(a, nsplit, s);
+      return;
+    }
+  }
   const int nsup = (a.N + GT<T>::ST - 1) / GT<T>::ST;
   dim3 grid(nsplit, npair);
   prof_begin("gram", s);

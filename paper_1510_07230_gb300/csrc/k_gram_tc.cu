@@ -1,0 +1,360 @@
+// Gram matrix of the FP32 form on the 5th-generation tensor cores
+// (Cholesky-QR, Sec. 3.2: S = <Wt^T Wt> of the trial block
+// Wt = (1 + tau sigma_i) w_i - tau hw_i, of the second-pass block, or of a
+// caller's block), for N <= 128 orbitals.
+//
+// Precision: every FP32 value x of the block is split into two TF32 numbers,
+// x = hi + lo + O(2^-22 x), hi = tf32(x), lo = tf32(x - hi).  Per K step two
+// MMAs of shape M = N = 128, K = 8 accumulate D += Hi Hi^T + Hi (2 Lo)^T, so
+// that the symmetric part (D + D^T) / 2 = Hi Hi^T + Hi Lo^T + Lo Hi^T is the
+// Gram to about 2^-21 relative per product (random sign); the reduction
+// kernel takes that symmetric part.  The tensor core adds into its FP32
+// accumulator with truncation, which biases long sums toward zero, so the
+// accumulator is restarted every PERIOD stages (64 grid points) and each
+// partial is added into a compensated pair (sum, error) that also lives in
+// tensor memory (TwoSum, round to nearest).  The diagonal, the one entry
+// whose products all have one sign, is summed exactly on the CUDA cores from
+// the FP32 values (double-float) and replaces the tensor-core diagonal.
+//
+// Roles (one CTA per SM, 416 threads):
+//   warps 0-3   promote the accumulator into the compensated pair (lane
+//               quadrant = warp) and write the split partial,
+//   warps 4-11  load W (and HW) from global memory, form Wt, split it into
+//               TF32 pairs, write the swizzled operand tiles and sum the
+//               diagonal,
+//   warp 12     allocates tensor memory; one lane issues the MMAs.
+// Stages of 32 grid points (one 128-byte row per orbital) pass through a
+// ring guarded by mbarriers; tensor memory holds two accumulators (double
+// buffer, so that promoting one period overlaps the MMAs of the next), the
+// sum and the error term: 4 x 128 of its 512 columns.
+#include "pou_internal.cuh"
+#include "tc_ptx.cuh"
+
+#include <algorithm>
+
+namespace pou {
+
+namespace {
+
+constexpr int KB = 32;               // grid points per stage (128 bytes per orbital row)
+constexpr int STAGES = 4;
+constexpr int PERIOD = 2;            // stages per tensor-memory accumulation period
+constexpr int EPI_WARPS = 4, PROD_WARPS = 8;
+constexpr int MMA_WARP = EPI_WARPS + PROD_WARPS;
+constexpr int NTHR = (MMA_WARP + 1) * 32;
+constexpr int NPROD = PROD_WARPS * 32;
+constexpr int TILE = 128 * 128;      // bytes: 128 rows x 128 bytes
+constexpr int STAGE_BYTES = 2 * TILE;  // hi tile, then 2*lo tile
+constexpr int OFF_DIAG = STAGES * STAGE_BYTES;  // 128 doubles
+constexpr int OFF_BAR = OFF_DIAG + 128 * 8;
+// barriers: full[STAGES], empty[STAGES], accf[2], acce[2], fin; then tmem slot, abort flag, coefs
+constexpr int NBAR = 2 * STAGES + 5;
+constexpr int OFF_MISC = OFF_BAR + NBAR * 8;
+constexpr int OFF_COEF = OFF_MISC + 16;
+constexpr int SMEM_BYTES = OFF_COEF + 128 * 4 + 1024;  // + alignment slack
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t COL_SUM = 256, COL_ERR = 384;
+constexpr uint32_t IDESC = tc::idesc_tf32(128, 128);
+
+static_assert(SMEM_BYTES <= 232448, "tensor-core Gram exceeds the shared-memory opt-in limit");
+
+__device__ unsigned int g_gram_tc_aborts = 0;
+
+__device__ __forceinline__ void two_sum_into(float& s, float& c, float v) {
+  const float t = s + v;
+  const float bp = t - s;
+  c += (s - (t - bp)) + (v - bp);
+  s = t;
+}
+
+__global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb) {
+  extern __shared__ unsigned char smem_raw[];
+  if (a.st && a.st->done) return;
+  if (!gate_open(a.st, a.gate)) return;
+
+  // 1024-byte aligned base for the swizzled operand tiles
+  const uint32_t raw_addr = tc::smem_u32(smem_raw);
+  const uint32_t pad = (1024u - (raw_addr & 1023u)) & 1023u;
+  unsigned char* smem = smem_raw + pad;
+  const uint32_t sbase = raw_addr + pad;
+  double* diag = reinterpret_cast<double*>(smem + OFF_DIAG);
+  const uint32_t bar0 = sbase + OFF_BAR;
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
+  auto accf_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
+  auto acce_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 + b); };
+  const uint32_t fin_bar = bar0 + 8u * (2 * STAGES + 4);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + OFF_MISC);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + OFF_MISC + 4);
+  float* coefs = reinterpret_cast<float*>(smem + OFF_COEF);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int N = a.N;
+  const i64 ng = a.ng;
+
+  // this CTA's contiguous range of stages
+  const i64 G = gridDim.x;
+  const i64 kb0 = nkb * (i64)blockIdx.x / G, kb1 = nkb * (i64)(blockIdx.x + 1) / G;
+  const int nmine = (int)(kb1 - kb0);
+  const int nper = (nmine + PERIOD - 1) / PERIOD;
+
+  const float* Wa;
+  const float* Ha = nullptr;
+  float tauF = 0.f;
+  if (a.trial) {
+    const int cur = a.st->cur;
+    Wa = a.W[cur];
+    Ha = a.HW[cur];
+    const double tau = a.st->tau_trial;
+    tauF = (float)tau;
+    for (int r = tid; r < 128; r += NTHR) coefs[r] = r < N ? (float)(1.0 + tau * a.sigma[cur][r]) : 0.f;
+  } else if (a.src_trial_slot) {
+    Wa = a.W[1 - a.st->cur];
+  } else {
+    Wa = a.A;
+  }
+  for (int r = tid; r < 128; r += NTHR) diag[r] = 0.0;
+  if (tid == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      tc::mbar_init(full_bar(s), NPROD);
+      tc::mbar_init(empty_bar(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(accf_bar(b), 1);
+      tc::mbar_init(acce_bar(b), EPI_WARPS * 32);
+    }
+    tc::mbar_init(fin_bar, 1);
+    *abort_flag = 0;
+    tc::mbar_init_fence();
+  }
+  if (warp == MMA_WARP) {
+    tc::tmem_alloc(tc::smem_u32(tmem_slot), TMEM_COLS);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp >= EPI_WARPS && warp < MMA_WARP) {
+    // ------------------------------------------------------------ producers
+    const int pt = tid - EPI_WARPS * 32;
+    const int c = pt & 7;         // 16-byte chunk of the row: points 4c .. 4c+3
+    const int r0 = pt >> 3;       // rows r0 + 32 q
+    const bool vec4 = (ng % 4 == 0) && ((reinterpret_cast<uintptr_t>(Wa) & 15u) == 0) &&
+                      (Ha == nullptr || (reinterpret_cast<uintptr_t>(Ha) & 15u) == 0);
+    float4 w[4], h[4], wn[4], hn[4];
+    float ds[4] = {0.f, 0.f, 0.f, 0.f}, dc[4] = {0.f, 0.f, 0.f, 0.f};  // diagonal, double-float
+    auto load = [&](i64 kb, float4 (&wv)[4], float4 (&hv)[4]) {
+      const i64 p = kb * KB + 4 * c;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = r0 + 32 * q;
+        wv[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        hv[q] = wv[q];
+        if (r >= N) continue;
+        const i64 off = (i64)r * ng + p;
+        if (vec4 && p + 3 < ng) {
+          wv[q] = __ldg(reinterpret_cast<const float4*>(Wa + off));
+          if (Ha) hv[q] = __ldg(reinterpret_cast<const float4*>(Ha + off));
+        } else {
+          float t[4] = {0.f, 0.f, 0.f, 0.f}, u[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (p + e < ng) {
+              t[e] = Wa[off + e];
+              if (Ha) u[e] = Ha[off + e];
+            }
+          wv[q] = make_float4(t[0], t[1], t[2], t[3]);
+          hv[q] = make_float4(u[0], u[1], u[2], u[3]);
+        }
+      }
+    };
+    if (nmine > 0) load(kb0, w, h);
+    for (int i = 0; i < nmine; ++i) {
+      if (i + 1 < nmine) load(kb0 + i + 1, wn, hn);
+      const int s = i % STAGES, n = i / STAGES;
+      if (n > 0 && !tc::mbar_wait(empty_bar(s), (n - 1) & 1, abort_flag)) break;
+      unsigned char* hi_t = smem + s * STAGE_BYTES;
+      unsigned char* lo_t = hi_t + TILE;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = r0 + 32 * q;
+        float x[4] = {w[q].x, w[q].y, w[q].z, w[q].w};
+        if (Ha) {
+          const float cf = coefs[r];
+          const float hv4[4] = {h[q].x, h[q].y, h[q].z, h[q].w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) x[e] = cf * x[e] - tauF * hv4[e];
+        }
+        float hi[4], lo[4], sq = 0.f;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          hi[e] = tc::to_tf32(x[e]);
+          lo[e] = 2.0f * tc::to_tf32(x[e] - hi[e]);
+          sq = fmaf(x[e], x[e], sq);
+        }
+        two_sum_into(ds[q], dc[q], sq);
+        const int off = r * 128 + ((c ^ (r & 7)) << 4);
+        *reinterpret_cast<float4*>(hi_t + off) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<float4*>(lo_t + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+      }
+      tc::fence_proxy_async_smem();
+      tc::mbar_arrive(full_bar(s));
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        w[q] = wn[q];
+        h[q] = hn[q];
+      }
+    }
+    // the eight lanes that share a row hold its diagonal in parts
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+#pragma unroll
+      for (int o = 1; o <= 4; o <<= 1) {
+        const float os = __shfl_xor_sync(0xffffffffu, ds[q], o);
+        const float oc = __shfl_xor_sync(0xffffffffu, dc[q], o);
+        two_sum_into(ds[q], dc[q], os);
+        dc[q] += oc;
+      }
+      if (c == 0) diag[r0 + 32 * q] = (double)ds[q] + (double)dc[q];
+    }
+  } else if (warp == MMA_WARP) {
+    // ------------------------------------------------------------ MMA issue
+    if (lane == 0) {
+      int it = 0;
+      bool ok = true, issued = false;
+      for (int per = 0; per < nper && ok; ++per) {
+        const int b = per & 1, use = per >> 1;
+        if (use > 0 && !tc::mbar_wait(acce_bar(b), (use - 1) & 1, abort_flag)) break;
+        tc::fence_after_sync();
+        const uint32_t d = tmem + (uint32_t)(b * 128);
+        const int end = std::min(nmine, it + PERIOD);
+        for (bool first = true; it < end; ++it, first = false) {
+          const int s = it % STAGES, n = it / STAGES;
+          if (!tc::mbar_wait(full_bar(s), n & 1, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t hi_a = sbase + (uint32_t)(s * STAGE_BYTES), lo_a = hi_a + TILE;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const uint64_t dh = tc::desc_sw128(hi_a + 32u * k), dl = tc::desc_sw128(lo_a + 32u * k);
+            tc::mma_tf32(d, dh, dh, IDESC, (first && k == 0) ? 0u : 1u);
+            tc::mma_tf32(d, dh, dl, IDESC, 1u);
+          }
+          issued = true;
+          tc::mma_commit(empty_bar(s));
+        }
+        if (ok) tc::mma_commit(accf_bar(b));
+      }
+      // every MMA issued has completed before tensor memory is released
+      if (issued) {
+        tc::mma_commit(fin_bar);
+        tc::mbar_wait(fin_bar, 0, abort_flag, 4000000000ull);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ promotion
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int per = 0; per < nper; ++per) {
+      const int b = per & 1, use = per >> 1;
+      if (!tc::mbar_wait(accf_bar(b), use & 1, abort_flag)) break;
+      tc::fence_after_sync();
+#pragma unroll 1
+      for (int c0 = 0; c0 < 128; c0 += 16) {
+        uint32_t x[16], sv[16], cv[16];
+        tc::tmem_ld16(lane_base + (uint32_t)(b * 128 + c0), x);
+        if (per > 0) {
+          tc::tmem_ld16(lane_base + COL_SUM + c0, sv);
+          tc::tmem_ld16(lane_base + COL_ERR + c0, cv);
+        }
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          float s = 0.f, e = 0.f;
+          if (per > 0) {
+            s = __uint_as_float(sv[j]);
+            e = __uint_as_float(cv[j]);
+          }
+          two_sum_into(s, e, __uint_as_float(x[j]));
+          sv[j] = __float_as_uint(s);
+          cv[j] = __float_as_uint(e);
+        }
+        tc::tmem_st16(lane_base + COL_SUM + c0, sv);
+        tc::tmem_st16(lane_base + COL_ERR + c0, cv);
+      }
+      tc::tmem_wait_st();
+      tc::fence_before_sync();
+      tc::mbar_arrive(acce_bar(b));
+    }
+  }
+
+  tc::fence_before_sync();
+  __syncthreads();
+  // split partial, stored transposed (the reduction symmetrises)
+  const bool bad = *abort_flag != 0;
+  double* out = a.split + (i64)blockIdx.x * (128 * 128);
+  if (warp < EPI_WARPS) {
+    tc::fence_after_sync();
+    const int row = tid;  // TMEM lane
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int c0 = 0; c0 < 128; c0 += 16) {
+      uint32_t sv[16], cv[16];
+      tc::tmem_ld16(lane_base + COL_SUM + c0, sv);
+      tc::tmem_ld16(lane_base + COL_ERR + c0, cv);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int col = c0 + j;
+        double v = (double)__uint_as_float(sv[j]) + (double)__uint_as_float(cv[j]);
+        if (nper == 0) v = 0.0;
+        if (col == row) v = diag[row];
+        if (bad) v = __longlong_as_double(0x7ff8000000000000ll);
+        out[(i64)col * 128 + row] = v;
+      }
+    }
+    tc::fence_before_sync();
+  }
+  __syncthreads();
+  if (warp == MMA_WARP) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, TMEM_COLS);
+  }
+  if (bad && tid == 0) {
+    atomicAdd(&g_gram_tc_aborts, 1u);
+    if (a.st) {
+      State* w = const_cast<State*>(a.st);
+      w->status = 3;  // POU_ECUDA: a pipeline wait gave up
+      w->done = 1;
+    }
+  }
+}
+
+bool g_configured = false;
+
+}  // namespace
+
+bool gram_tc_eligible(const GramArgs<float>& a) {
+  return a.B == nullptr && !a.src_cur_pair && a.N >= 1 && a.N <= 128;
+}
+
+void configure_gram_tc() {
+  if (g_configured) return;
+  cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  g_configured = true;
+}
+
+void launch_gram_tc(const GramArgs<float>& a, int nsplit, cudaStream_t s) {
+  configure_gram_tc();
+  const i64 nkb = (a.ng + KB - 1) / KB;
+  prof_begin("gram", s);
+  // one split per CTA; a CTA without stages writes zeros
+  k_gram_tc<<<nsplit, NTHR, SMEM_BYTES, s>>>(a, nkb);
+  prof_end(s);
+}
+
+}  // namespace pou

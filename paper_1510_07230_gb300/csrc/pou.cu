@@ -794,6 +794,7 @@ void pou::configure_kernels() {
   configure_fft();
   configure_eigh();
   configure_apply_h();
+  configure_gram_tc();
   done = true;
 }
 

@@ -111,6 +111,13 @@ void launch_gram(const GramArgs<T>& a, cudaStream_t s);
 template <typename T>
 void launch_gram_nsplit(const GramArgs<T>& a, int nsplit, cudaStream_t s);
 
+// FP32 Gram on the tensor cores (TF32 split products), N <= 128, symmetric
+// modes only; writes the same [nsplit][128 * 128] split layout (transposed
+// and unsymmetrised: the reduction takes the symmetric part).
+bool gram_tc_eligible(const GramArgs<float>& a);
+void launch_gram_tc(const GramArgs<float>& a, int nsplit, cudaStream_t s);
+void configure_gram_tc();
+
 struct GramReduceArgs {
   const State* st;
   const double* split;

@@ -49,6 +49,8 @@ WORKLOADS = {
     "l20_g96_n32": Workload("l20_g96_n32", 20.0, 96, 2, 16, "uniform26", 32, 1000, 3),
     # headline: L=30, 160^3, 13-point, 64 atoms Z~U[2,6], N=128
     "l30_g160_n128": Workload("l30_g160_n128", 30.0, 160, 4, 64, "uniform26", 128, 2000, 4),
+    # reduced headline system for hardware-counter captures (block > L2, a few GB on the device)
+    "l24_g128_n64": Workload("l24_g128_n64", 24.0, 128, 4, 32, "uniform26", 64, 100, 6),
     # large: L=40, 192^3, 13-point, 256 atoms Z~U[2,6], N=512, 100 iterations
     "l40_g192_n512": Workload("l40_g192_n512", 40.0, 192, 4, 256, "uniform26", 512, 100, 5),
 }

@@ -61,6 +61,27 @@ def test_gram_op(P, dt, N, ng):
     assert err < (1e-13 if dt == "f64" else 2e-6), err
 
 
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+@pytest.mark.parametrize("N,ng", [(16, 40000), (128, 160 ** 3 // 8)])
+def test_gram_op_coherent_sums(P, dt, N, ng):
+    # rows sharing one positive component: every off-diagonal entry is a sum
+    # of products of one sign, the case where a biased accumulation shows
+    rng = np.random.default_rng(N + 3 * ng)
+    A = 1.0 + 0.3 * rng.standard_normal((N, ng)) + 0.2 * rng.random((N, 1))
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    Ad = dev(A, tdt)
+    code = P.DT_F64 if dt == "f64" else P.DT_F32
+    ws = torch.empty(P.gram_workspace_bytes(code, ng, N) // 8 + 1, dtype=torch.float64, device="cuda")
+    S = torch.empty((N, N), dtype=torch.float64, device="cuda")
+    P.gram(Ad, 1.0 / ng, S, ws)
+    Ar = Ad.double().cpu().numpy()
+    ref = (Ar @ Ar.T) / ng
+    err = np.max(np.abs(S.cpu().numpy() - ref) / np.abs(ref))
+    assert err < (1e-13 if dt == "f64" else 1e-6), err
+    d = np.abs(np.diag(S.cpu().numpy()) - np.diag(ref)) / np.diag(ref)
+    assert np.max(d) < (1e-13 if dt == "f64" else 1e-9), np.max(d)
+
+
 # ------------------------------------------------------------------ a4: Cholesky / inverse
 @pytest.mark.parametrize("N", [1, 7, 64, 100, 128])
 def test_cholinv_op(P, N):
