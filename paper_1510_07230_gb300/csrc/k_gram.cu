@@ -2,14 +2,14 @@
 //   * Gram S = <Wt^T Wt> of the trial block Wt = W - tau Z
 //     = (1 + tau sigma_i) w_i - tau hw_i, formed on the fly from W and HW
 //     (so Z is never stored), split over the grid dimension with one FP64
-//     partial per split and a deterministic reduction;
+//     partial per split and a deterministic reduction (FP64 form, and the
+//     general product A^T B of either form; the symmetric FP32 Gram runs on
+//     the tensor cores, k_gram_tc.cu);
+//   * the reduction of the split partials, with the exact FP64 diagonal of
+//     the trial Gram from the H-apply sums;
 //   * rotation W_new = Wt R^-1 (R^-1 upper triangular) fused with the
-//     density rho = f sum_j w_new_j^2.
-// In the FP32 form every product is an FP32 FMA (round to nearest); the
-// split partials are FP64.  The coefficients (1 + tau sigma_i) and tau are
-// rounded to the working type once and the same rounded values are used by
-// the Gram, the exact FP64 Gram diagonal and the rotation, so that the
-// normalisation of every new orbital is consistent to FP64 accuracy.
+//     density rho = f sum_j w_new_j^2 (FP64 form; the FP32 form runs on the
+//     tensor cores, k_rotate_tc.cu).
 #include "pou_internal.cuh"
 
 #include <algorithm>
@@ -50,27 +50,6 @@ __device__ __forceinline__ void add_square(F2& a, float x) {
   two_sum_add(a, p, fmaf(x, x, -p));
 }
 __device__ __forceinline__ void add_f2(F2& a, const F2& b) { two_sum_add(a, b.s, b.c); }
-
-// 32-bit integer mixer "lowbias32" (C. Wellons, hash-prospector), used as a
-// counter-based source of uniform bits for the dithered rounding below.
-__device__ __forceinline__ unsigned mix32(unsigned x) {
-  x ^= x >> 16;
-  x *= 0x7feb352dU;
-  x ^= x >> 15;
-  x *= 0x846ca68bU;
-  x ^= x >> 16;
-  return x;
-}
-
-// Unbiased rounding: fma(a, x, rest + d) with d uniform in (-ulp/2, ulp/2)
-// of the result rounds a x + rest up or down with probabilities that make
-// the expected stored value exact.  Near convergence the corrections that
-// keep an orbital normalised are below half an ulp of every element, and
-// plain round-to-nearest would drop them all the same way.
-__device__ __forceinline__ float dither(float x, unsigned byte) {
-  const float ulp = __uint_as_float(__float_as_uint(x) & 0x7f800000u) * 1.1920928955078125e-7f;
-  return ((float)byte * (1.0f / 256.0f) - 0.498046875f) * ulp;
-}
 
 // Gram of a block over the grid dimension.  Work unit: a tile of BK
 // consecutive grid points; CTA b of G takes tiles b, b + G, b + 2G, ...
@@ -268,59 +247,48 @@ __global__ void k_gram_reduce(GramReduceArgs a) {
     const double zz = pp[P_ZZ] - 2.0 * d * pp[P_ZW] + d * d * pp[P_WW];
     s = a.dV * (pp[P_WW] - 2.0 * t * wz + t * t * zz);
   }
-  if (a.normpart && r == c) {
-    // column norms of the block, summed without cancellation by the
-    // rotation that produced it
-    double t = 0.0;
-    for (int k = 0; k < a.nnorm; ++k) t += a.normpart[(i64)k * N + r];
-    s = a.dV * t;
-  }
   a.S[(i64)r * N + c] = s;
   if (!a.general) a.S[(i64)c * N + r] = s;
 }
 
 // --------------------------------------------------------------- rotation
+// FP64 form (the FP32 form runs on the tensor cores, k_rotate_tc.cu):
+// W_new = X R^-1 with X = Wt (trial) or the block itself, fused with the
+// density.  A chunk of RP points of all N orbitals is staged in shared
+// memory; each thread forms 8 outputs x 4 points.  For the upper-triangular
+// R^-1 only i <= j contributes.
 constexpr int RNT = 256;
 constexpr int RP = 64;  // points per chunk
 
-template <typename T>
-__global__ void __launch_bounds__(RNT) k_rotate(RotArgs<T> a, int nchunks) {
+__global__ void __launch_bounds__(RNT) k_rotate(RotArgs<double> a, int nchunks) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N = a.N;
   const int NPAD = 128;
-  T* Rs = reinterpret_cast<T*>(smem_raw);                 // [NPAD][NPAD]
-  T* Xs = Rs + NPAD * NPAD;                               // [NPAD][RP + 4]
-  T* Rlo = Xs + NPAD * (RP + 4);                          // [NPAD] low part of the diagonal
-  T* coefs = Rlo + NPAD;                                  // [NPAD]
-  float* self = reinterpret_cast<float*>(coefs + NPAD);   // [4][NPAD]: A_hi, A_lo, B_hi, B_lo
+  double* Rs = reinterpret_cast<double*>(smem_raw);  // [NPAD][NPAD]
+  double* Xs = Rs + NPAD * NPAD;                      // [NPAD][RP + 4]
+  double* coefs = Xs + NPAD * (RP + 4);               // [NPAD]
   constexpr int XS = RP + 4;
-  // FP32 form: the self term of output j, A_j w_j - B_j h_j with FP64 A, B
-  // (trial: A = R_jj (1 + tau sigma_j), B = R_jj tau; otherwise A = R_jj, B = 0),
-  // is summed exactly with the off-diagonal part and stored by unbiased rounding.
-  constexpr bool kExactSelf = (sizeof(T) == 4);
 
   if (a.st && a.st->done) return;
   if (!gate_open(a.st, a.gate)) return;
   const int tid = threadIdx.x;
-  int cur = 0;
-  const T* Wsrc;
-  const T* Hsrc = nullptr;
-  T* out;
+  const double* Wsrc;
+  const double* Hsrc = nullptr;
+  double* out;
   double* rho;
-  T tauT = T(0);
+  double tau = 0.0;
   if (a.trial) {
-    cur = a.st->cur;
+    const int cur = a.st->cur;
     Wsrc = a.W[cur];
     Hsrc = a.HW[cur];
     out = a.Wout[1 - cur];
     rho = a.rho[1 - cur];
-    const double tau = a.st->tau_trial;
-    tauT = (T)tau;
-    for (int i = tid; i < NPAD; i += RNT) coefs[i] = i < N ? (T)(1.0 + tau * a.sigma[cur][i]) : T(0);
+    tau = a.st->tau_trial;
+    for (int i = tid; i < NPAD; i += RNT) coefs[i] = i < N ? 1.0 + tau * a.sigma[cur][i] : 0.0;
   } else if (a.st) {
-    cur = a.st->cur;
-    // in-place second pass reads the block it overwrites: every chunk is
-    // staged in shared memory before any of its outputs is stored
+    const int cur = a.st->cur;
+    // in-place passes read the block they overwrite: every chunk is staged in
+    // shared memory before any of its outputs is stored
     if (a.src_cur_slot) {
       Wsrc = a.Wout[cur];
       out = a.Wout[cur];
@@ -337,29 +305,9 @@ __global__ void __launch_bounds__(RNT) k_rotate(RotArgs<T> a, int nchunks) {
   }
   for (int idx = tid; idx < NPAD * NPAD; idx += RNT) {
     const int i = idx / NPAD, j = idx % NPAD;
-    const double v = (i < N && j < N) ? a.Rinv[(i64)i * N + j] : 0.0;
-    Rs[idx] = (kExactSelf && i == j) ? T(0) : (T)v;
-    if (i == j) {
-      Rlo[i] = kExactSelf ? T(0) : (T)(v - (double)(T)v);
-      if (kExactSelf) {
-        double A = v, B = 0.0;
-        if (a.trial && i < N) {
-          const double tau = a.st->tau_trial;
-          A = v * (1.0 + tau * a.sigma[a.st->cur][i]);
-          B = v * tau;
-        }
-        const float ah = (float)A, bh = (float)B;
-        self[i] = ah;
-        self[NPAD + i] = (float)(A - (double)ah);
-        self[2 * NPAD + i] = bh;
-        self[3 * NPAD + i] = (float)(B - (double)bh);
-      }
-    }
+    Rs[idx] = (i < N && j < N) ? a.Rinv[(i64)i * N + j] : 0.0;
   }
   __syncthreads();
-  // counter for the unbiased rounding: one stream per pass and per use
-  const unsigned seed32 = mix32((unsigned)(a.st ? a.st->passes : 0) * 4u + (unsigned)a.sr_salt + 0x85ebca6bu);
-  const bool vec4 = (a.ng % 4) == 0;  // 16-byte aligned rows of four points
 
   const int lane = tid & 31, warp = tid >> 5;
   const int jw = warp & 3, pw = warp >> 2;
@@ -368,50 +316,28 @@ __global__ void __launch_bounds__(RNT) k_rotate(RotArgs<T> a, int nchunks) {
   const int pl0 = pw * 32 + pg * 4; // 4 points within the chunk
   const int imax = a.general ? N : min(N, j0 + 8);
   const i64 ng = a.ng;
-  // compensated (Kahan) per-CTA column norms, held by the pg == 0 lanes
-  float nh[8], nc[8];
-#pragma unroll
-  for (int jj = 0; jj < 8; ++jj) nh[jj] = nc[jj] = 0.f;
 
   for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const i64 p0 = (i64)ch * RP;
-    if (sizeof(T) == 4 && vec4 && p0 + RP <= ng) {
-      // four points per load
-      for (int idx = tid; idx < N * (RP / 4); idx += RNT) {
-        const int i = idx / (RP / 4), pp = 4 * (idx % (RP / 4));
-        const i64 off = (i64)i * ng + p0 + pp;
-        float4 v = *reinterpret_cast<const float4*>(&Wsrc[off]);
-        if (a.trial) {
-          const float4 h = *reinterpret_cast<const float4*>(&Hsrc[off]);
-          const float cf = (float)coefs[i], tf = (float)tauT;
-          v.x = cf * v.x - tf * h.x;
-          v.y = cf * v.y - tf * h.y;
-          v.z = cf * v.z - tf * h.z;
-          v.w = cf * v.w - tf * h.w;
-        }
-        *reinterpret_cast<float4*>(&Xs[i * XS + pp]) = v;
+    for (int idx = tid; idx < N * RP; idx += RNT) {
+      const int i = idx / RP, pp = idx % RP;
+      const i64 gp = p0 + pp;
+      double v = 0.0;
+      if (gp < ng) {
+        const i64 off = (i64)i * ng + gp;
+        v = a.trial ? coefs[i] * Wsrc[off] - tau * Hsrc[off] : Wsrc[off];
       }
-    } else {
-      for (int idx = tid; idx < N * RP; idx += RNT) {
-        const int i = idx / RP, pp = idx % RP;
-        const i64 gp = p0 + pp;
-        T v = T(0);
-        if (gp < ng) {
-          const i64 off = (i64)i * ng + gp;
-          v = a.trial ? coefs[i] * Wsrc[off] - tauT * Hsrc[off] : Wsrc[off];
-        }
-        Xs[i * XS + pp] = v;
-      }
+      Xs[i * XS + pp] = v;
     }
     __syncthreads();
 
-    T acc[8][4];
+    double acc[8][4];
 #pragma unroll
     for (int jj = 0; jj < 8; ++jj)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[jj][q] = T(0);
+      for (int q = 0; q < 4; ++q) acc[jj][q] = 0.0;
     for (int i = 0; i < imax; ++i) {
-      T rv[8], xv[4];
+      double rv[8], xv[4];
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj) rv[jj] = Rs[i * NPAD + j0 + jj];
 #pragma unroll
@@ -421,125 +347,39 @@ __global__ void __launch_bounds__(RNT) k_rotate(RotArgs<T> a, int nchunks) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[jj][q] = fma(rv[jj], xv[q], acc[jj][q]);
     }
-    // low part of the diagonal of R^-1 (zero in FP64)
-#pragma unroll
-    for (int jj = 0; jj < 8; ++jj) {
-      const int j = j0 + jj;
-      if (j < N) {
-        const T lo = Rlo[j];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[jj][q] = fma(lo, Xs[j * XS + pl0 + q], acc[jj][q]);
-      }
-    }
-    if (kExactSelf) {
-#pragma unroll
-      for (int jj = 0; jj < 8; ++jj) {
-        const int j = j0 + jj;
-        if (j >= N) continue;
-        const float ah = self[j], al = self[NPAD + j], bh = self[2 * NPAD + j], bl = self[3 * NPAD + j];
-        const unsigned bits = mix32(seed32 ^ mix32((unsigned)j * 0x9e3779b1u ^ (unsigned)(p0 + pl0)));
-        float wv[4] = {0.f, 0.f, 0.f, 0.f}, hv[4] = {0.f, 0.f, 0.f, 0.f};
-        const i64 g0 = p0 + pl0;
-        if (a.trial) {
-          if (vec4 && g0 + 3 < ng) {
-            const float4 w4 = *reinterpret_cast<const float4*>(&Wsrc[(i64)j * ng + g0]);
-            const float4 h4 = *reinterpret_cast<const float4*>(&Hsrc[(i64)j * ng + g0]);
-            wv[0] = w4.x; wv[1] = w4.y; wv[2] = w4.z; wv[3] = w4.w;
-            hv[0] = h4.x; hv[1] = h4.y; hv[2] = h4.z; hv[3] = h4.w;
-          } else {
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-              if (g0 + q < ng) {
-                wv[q] = (float)Wsrc[(i64)j * ng + g0 + q];
-                hv[q] = (float)Hsrc[(i64)j * ng + g0 + q];
-              }
-          }
-        } else {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) wv[q] = (float)Xs[j * XS + pl0 + q];
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float d = dither(wv[q], (bits >> (8 * q)) & 0xffu);
-          const float rest = fmaf(al, wv[q], fmaf(-bl, hv[q], (float)acc[jj][q] + d));
-          acc[jj][q] = (T)fmaf(ah, wv[q], fmaf(-bh, hv[q], rest));
-        }
-      }
-    }
-    // store and density (FP32 form: double-float sums of squares)
-    F2 sq[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) sq[q].s = sq[q].c = 0.f;
     double sqd[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
     for (int jj = 0; jj < 8; ++jj) {
       const int j = j0 + jj;
-      float col = 0.f;
       if (j < N) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const i64 gp = p0 + pl0 + q;
           if (gp < ng) out[(i64)j * ng + gp] = acc[jj][q];
-          if (sizeof(T) == 8)
-            sqd[q] += (double)acc[jj][q] * (double)acc[jj][q];
-          else
-            add_square(sq[q], (float)acc[jj][q]);
-          col = fmaf((float)acc[jj][q], (float)acc[jj][q], col);  // points past ng hold 0
+          sqd[q] = fma(acc[jj][q], acc[jj][q], sqd[q]);
         }
-      }
-      if (a.normpart) {
-        col += __shfl_xor_sync(0xffffffffu, col, 4);
-        col += __shfl_xor_sync(0xffffffffu, col, 8);
-        col += __shfl_xor_sync(0xffffffffu, col, 16);
-        const float y = col - nc[jj];
-        const float t = nh[jj] + y;
-        nc[jj] = (t - nh[jj]) - y;
-        nh[jj] = t;
       }
     }
     if (rho != nullptr) {
-      if (sizeof(T) == 8) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          sqd[q] += __shfl_xor_sync(0xffffffffu, sqd[q], 1);
-          sqd[q] += __shfl_xor_sync(0xffffffffu, sqd[q], 2);
-        }
-      } else {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          for (int o = 1; o <= 2; o <<= 1) {
-            F2 other;
-            other.s = __shfl_xor_sync(0xffffffffu, sq[q].s, o);
-            other.c = __shfl_xor_sync(0xffffffffu, sq[q].c, o);
-            add_f2(sq[q], other);
-          }
-        }
+      for (int q = 0; q < 4; ++q) {
+        sqd[q] += __shfl_xor_sync(0xffffffffu, sqd[q], 1);
+        sqd[q] += __shfl_xor_sync(0xffffffffu, sqd[q], 2);
       }
     }
     __syncthreads();  // Xs no longer read; reuse a region for the density
     if (rho != nullptr) {
-      double* dsum = reinterpret_cast<double*>(Xs);  // [4][RP]
+      double* dsum = Xs;  // [4][RP]
       if (jg == 0) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          dsum[jw * RP + pl0 + q] = (sizeof(T) == 8) ? sqd[q] : (double)sq[q].s + (double)sq[q].c;
+        for (int q = 0; q < 4; ++q) dsum[jw * RP + pl0 + q] = sqd[q];
       }
       __syncthreads();
       if (tid < RP) {
         const i64 gp = p0 + tid;
-        if (gp < ng) {
-          const double s = dsum[tid] + dsum[RP + tid] + dsum[2 * RP + tid] + dsum[3 * RP + tid];
-          rho[gp] = F_OCC * s;
-        }
+        if (gp < ng) rho[gp] = F_OCC * (dsum[tid] + dsum[RP + tid] + dsum[2 * RP + tid] + dsum[3 * RP + tid]);
       }
       __syncthreads();
-    }
-  }
-  if (a.normpart && pg == 0) {
-#pragma unroll
-    for (int jj = 0; jj < 8; ++jj) {
-      const int j = j0 + jj;
-      if (j < N) a.normpart[((i64)blockIdx.x * 2 + pw) * N + j] = (double)nh[jj] - (double)nc[jj];
     }
   }
 }
@@ -665,31 +505,31 @@ void launch_gram_reduce(const GramReduceArgs& a, cudaStream_t s) {
   prof_end(s);
 }
 
-template <typename T>
 static size_t rotate_smem() {
   const int NPAD = 128;
-  return sizeof(T) * ((size_t)NPAD * NPAD + (size_t)NPAD * (RP + 4) + 2 * NPAD) + sizeof(float) * 4 * NPAD;
+  return sizeof(double) * ((size_t)NPAD * NPAD + (size_t)NPAD * (RP + 4) + NPAD);
 }
 
 void configure_rotate() {
-  cudaFuncSetAttribute(k_rotate<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rotate_smem<float>());
-  cudaFuncSetAttribute(k_rotate<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rotate_smem<double>());
+  cudaFuncSetAttribute(k_rotate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rotate_smem());
 }
 
 int rotate_grid(i64 ng, int elem_bytes) {
+  if (elem_bytes == 4) return rotate_tc_grid(ng);
   const int nchunks = (int)((ng + RP - 1) / RP);
-  const int per_sm = elem_bytes == 4 ? 2 : 1;
-  return std::min(nchunks, 152 * per_sm);
+  return std::min(nchunks, 152);
 }
 
 template <typename T>
 void launch_rotate(const RotArgs<T>& a, cudaStream_t s) {
-  const size_t smem = rotate_smem<T>();
-  const int nchunks = (int)((a.ng + RP - 1) / RP);
-  const int grid = rotate_grid(a.ng, (int)sizeof(T));
-  prof_begin("rotate_density", s);
-  k_rotate<T><<<grid, RNT, smem, s>>>(a, nchunks);
-  prof_end(s);
+  if constexpr (sizeof(T) == 4) {
+    launch_rotate_tc(a, s);
+  } else {
+    const int nchunks = (int)((a.ng + RP - 1) / RP);
+    prof_begin("rotate_density", s);
+    k_rotate<<<rotate_grid(a.ng, 8), RNT, rotate_smem(), s>>>(a, nchunks);
+    prof_end(s);
+  }
 }
 template void launch_rotate<float>(const RotArgs<float>&, cudaStream_t);
 template void launch_rotate<double>(const RotArgs<double>&, cudaStream_t);

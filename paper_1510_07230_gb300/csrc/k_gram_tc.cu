@@ -16,12 +16,14 @@
 // whose products all have one sign, is summed exactly on the CUDA cores from
 // the FP32 values (double-float) and replaces the tensor-core diagonal.
 //
-// Roles (one CTA per SM, 416 threads):
-//   warps 0-3   promote the accumulator into the compensated pair (lane
-//               quadrant = warp) and write the split partial,
-//   warps 4-11  load W (and HW) from global memory, form Wt, split it into
-//               TF32 pairs, write the swizzled operand tiles and sum the
-//               diagonal,
+// Roles (one CTA per SM, 416 threads: 13 warps, at most four per SM
+// sub-partition, so that each thread may hold 128 registers):
+//   warps 0-7   load W (and HW) from global memory two stages ahead (so that
+//               each SM keeps two stages of loads in flight), form Wt, split
+//               it into TF32 pairs, write the swizzled operand tiles and sum
+//               the diagonal;
+//   warps 8-11  promote the accumulator into the compensated pair (TMEM lane
+//               quadrant = warp - 8) and write the split partial;
 //   warp 12     allocates tensor memory; one lane issues the MMAs.
 // Stages of 32 grid points (one 128-byte row per orbital) pass through a
 // ring guarded by mbarriers; tensor memory holds two accumulators (double
@@ -39,8 +41,9 @@ namespace {
 constexpr int KB = 32;               // grid points per stage (128 bytes per orbital row)
 constexpr int STAGES = 4;
 constexpr int PERIOD = 2;            // stages per tensor-memory accumulation period
-constexpr int EPI_WARPS = 4, PROD_WARPS = 8;
-constexpr int MMA_WARP = EPI_WARPS + PROD_WARPS;
+constexpr int PROD_WARPS = 8, EPI_WARPS = 4;
+constexpr int EPI0 = PROD_WARPS;     // first promotion warp
+constexpr int MMA_WARP = PROD_WARPS + EPI_WARPS;
 constexpr int NTHR = (MMA_WARP + 1) * 32;
 constexpr int NPROD = PROD_WARPS * 32;
 constexpr int TILE = 128 * 128;      // bytes: 128 rows x 128 bytes
@@ -67,6 +70,9 @@ __device__ __forceinline__ void two_sum_into(float& s, float& c, float v) {
   s = t;
 }
 
+// VEC: rows start on 16-byte boundaries and ng % 4 == 0 (float4 loads); the
+// other instantiation loads element by element.
+template <bool VEC>
 __global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb) {
   extern __shared__ unsigned char smem_raw[];
   if (a.st && a.st->done) return;
@@ -136,14 +142,11 @@ __global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb)
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp >= EPI_WARPS && warp < MMA_WARP) {
+  if (warp < PROD_WARPS) {
     // ------------------------------------------------------------ producers
-    const int pt = tid - EPI_WARPS * 32;
+    const int pt = tid;
     const int c = pt & 7;         // 16-byte chunk of the row: points 4c .. 4c+3
     const int r0 = pt >> 3;       // rows r0 + 32 q
-    const bool vec4 = (ng % 4 == 0) && ((reinterpret_cast<uintptr_t>(Wa) & 15u) == 0) &&
-                      (Ha == nullptr || (reinterpret_cast<uintptr_t>(Ha) & 15u) == 0);
-    float4 w[4], h[4], wn[4], hn[4];
     float ds[4] = {0.f, 0.f, 0.f, 0.f}, dc[4] = {0.f, 0.f, 0.f, 0.f};  // diagonal, double-float
     auto load = [&](i64 kb, float4 (&wv)[4], float4 (&hv)[4]) {
       const i64 p = kb * KB + 4 * c;
@@ -154,9 +157,12 @@ __global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb)
         hv[q] = wv[q];
         if (r >= N) continue;
         const i64 off = (i64)r * ng + p;
-        if (vec4 && p + 3 < ng) {
-          wv[q] = __ldg(reinterpret_cast<const float4*>(Wa + off));
-          if (Ha) hv[q] = __ldg(reinterpret_cast<const float4*>(Ha + off));
+        if (VEC) {
+          // ng % 4 == 0: a chunk is either wholly inside the row or past its end
+          if (p < ng) {
+            wv[q] = __ldg(reinterpret_cast<const float4*>(Wa + off));
+            if (Ha) hv[q] = __ldg(reinterpret_cast<const float4*>(Ha + off));
+          }
         } else {
           float t[4] = {0.f, 0.f, 0.f, 0.f}, u[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -170,11 +176,12 @@ __global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb)
         }
       }
     };
-    if (nmine > 0) load(kb0, w, h);
-    for (int i = 0; i < nmine; ++i) {
-      if (i + 1 < nmine) load(kb0 + i + 1, wn, hn);
+    // one stage: loads for stage i + 2 go into the register set that held
+    // stage i - 1; stage i is written from (w, h)
+    auto step = [&](int i, const float4 (&w)[4], const float4 (&h)[4], float4 (&wl)[4], float4 (&hl)[4]) -> bool {
+      if (i + 2 < nmine) load(kb0 + i + 2, wl, hl);
       const int s = i % STAGES, n = i / STAGES;
-      if (n > 0 && !tc::mbar_wait(empty_bar(s), (n - 1) & 1, abort_flag)) break;
+      if (n > 0 && !tc::mbar_wait(empty_bar(s), (n - 1) & 1, abort_flag)) return false;
       unsigned char* hi_t = smem + s * STAGE_BYTES;
       unsigned char* lo_t = hi_t + TILE;
 #pragma unroll
@@ -201,11 +208,15 @@ __global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb)
       }
       tc::fence_proxy_async_smem();
       tc::mbar_arrive(full_bar(s));
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        w[q] = wn[q];
-        h[q] = hn[q];
-      }
+      return true;
+    };
+    float4 wA[4], hA[4], wB[4], hB[4], wC[4], hC[4];
+    if (nmine > 0) load(kb0, wA, hA);
+    if (nmine > 1) load(kb0 + 1, wB, hB);
+    for (int i = 0; i < nmine; i += 3) {
+      if (!step(i, wA, hA, wC, hC)) break;
+      if (i + 1 >= nmine || !step(i + 1, wB, hB, wA, hA)) break;
+      if (i + 2 >= nmine || !step(i + 2, wC, hC, wB, hB)) break;
     }
     // the eight lanes that share a row hold its diagonal in parts
 #pragma unroll
@@ -258,7 +269,8 @@ __global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb)
     __syncwarp();
   } else {
     // ------------------------------------------------------------ promotion
-    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    const int quad = warp - EPI0;
+    const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
     for (int per = 0; per < nper; ++per) {
       const int b = per & 1, use = per >> 1;
       if (!tc::mbar_wait(accf_bar(b), use & 1, abort_flag)) break;
@@ -297,10 +309,11 @@ __global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb)
   // split partial, stored transposed (the reduction symmetrises)
   const bool bad = *abort_flag != 0;
   double* out = a.split + (i64)blockIdx.x * (128 * 128);
-  if (warp < EPI_WARPS) {
+  if (warp >= EPI0 && warp < MMA_WARP) {
     tc::fence_after_sync();
-    const int row = tid;  // TMEM lane
-    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    const int quad = warp - EPI0;
+    const int row = quad * 32 + lane;  // TMEM lane
+    const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
 #pragma unroll 1
     for (int c0 = 0; c0 < 128; c0 += 16) {
       uint32_t sv[16], cv[16];
@@ -344,7 +357,8 @@ bool gram_tc_eligible(const GramArgs<float>& a) {
 
 void configure_gram_tc() {
   if (g_configured) return;
-  cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  cudaFuncSetAttribute(k_gram_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  cudaFuncSetAttribute(k_gram_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   g_configured = true;
 }
 
@@ -353,7 +367,18 @@ void launch_gram_tc(const GramArgs<float>& a, int nsplit, cudaStream_t s) {
   const i64 nkb = (a.ng + KB - 1) / KB;
   prof_begin("gram", s);
   // one split per CTA; a CTA without stages writes zeros
-  k_gram_tc<<<nsplit, NTHR, SMEM_BYTES, s>>>(a, nkb);
+  // the source rows of the mode: W[cur] and HW[cur] (trial), W[1 - cur], or A
+  bool vec = (a.ng % 4) == 0;
+  auto aligned = [](const float* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  if (a.trial || a.src_trial_slot) {
+    for (int k = 0; k < 2; ++k) vec = vec && aligned(a.W[k]) && (!a.trial || aligned(a.HW[k]));
+  } else {
+    vec = vec && aligned(a.A);
+  }
+  if (vec)
+    k_gram_tc<true><<<nsplit, NTHR, SMEM_BYTES, s>>>(a, nkb);
+  else
+    k_gram_tc<false><<<nsplit, NTHR, SMEM_BYTES, s>>>(a, nkb);
   prof_end(s);
 }
 

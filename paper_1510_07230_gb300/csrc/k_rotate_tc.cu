@@ -1,0 +1,468 @@
+// Rotation W_new = Wt R^-1 of the FP32 form (Orth by Cholesky-QR, Sec. 3.2;
+// the subspace rotation W P of Algorithm M, Sec. 3.3) on the 5th-generation
+// tensor cores, fused with the density rho = f sum_j w_new_j^2 (Sec. 2), for
+// N <= 128 orbitals.
+//
+// Split of the work.  Output j at point p is
+//   w_new_j(p) = sum_{i != j} x_i(p) R_ij  +  R_jj x_j(p),
+// x = Wt (trial: (1 + tau sigma_i) w_i - tau hw_i) or the block itself.  The
+// off-diagonal sum runs on the tensor cores as D = X R_off with M = 128 grid
+// points (tensor-memory lanes), N = 128 outputs j (columns) and K = 128
+// orbitals i, both operands split into TF32 pairs: D = Xhi Rhi + Xhi Rlo +
+// Xlo Rhi, which carries the sum to about 2^-21 of its own size.  The tensor
+// core adds into its FP32 accumulator with truncation (a bias toward zero of
+// a fraction of an ulp per accumulation), so the dominant Xhi Rhi part is
+// kept in two accumulators (orbitals 0-63 and 64-127, eight accumulations
+// each), the small cross terms in a third, and the three are added on the
+// CUDA cores with round-to-nearest.  The self term is formed on the CUDA
+// cores from w and hw directly with double-float coefficients and stored
+// with unbiased (dithered) rounding, as the CUDA-core rotation does, because
+// near convergence the corrections that keep each orbital normalised are
+// below half an ulp of its elements.
+//
+// With points on the lanes, every global access of the epilogue (w, hw of
+// the self term, the output, the density) is one 128-byte segment of one row
+// per warp instruction, and the density of a point is a per-thread sum.
+//
+// Pipeline per tile of 128 points (one CTA per SM, 512 threads: 16 warps,
+// four per SM sub-partition, so that each thread may hold 128 registers):
+//   warps 0-7   (producers) load one 32-orbital K atom of the tile at a time
+//               (eight lanes per 128-byte row segment), two atoms ahead so
+//               that each SM keeps two atoms of loads in flight, form Wt,
+//               split, and write it K-major (128-byte swizzle) into one of
+//               two atom slots; warp 0 also allocates tensor memory, and its
+//               lane 0 issues the MMAs of an atom once all producers wrote it;
+//   warps 8-15  (epilogue; two warps per TMEM lane quadrant, 64 output
+//               columns each) add the three accumulators into the 128 free
+//               tensor-memory columns and release them at once, so the next
+//               tile's MMAs overlap the rest: the self term (w and hw read in
+//               8-column groups, the next group's loads in flight while one
+//               is finished), the stores and the squares for the density.
+// Tile rows are permuted within each 32-point group (row 8e + q holds point
+// 4q + e) so that the producers' transposing shared-memory stores hit 32
+// distinct banks.
+#include "pou_internal.cuh"
+#include "tc_ptx.cuh"
+
+#include <algorithm>
+
+namespace pou {
+
+namespace {
+
+constexpr int TPTS = 128;                  // points per tile (= M)
+constexpr int PROD_WARPS = 8, EPI_WARPS = 8;
+constexpr int EPI0 = PROD_WARPS;           // first epilogue warp
+constexpr int NTHR = (EPI0 + EPI_WARPS) * 32;
+constexpr int ATOM = 128 * 128;            // bytes of one K atom: 128 rows x 128 bytes
+constexpr int SLOT = 2 * ATOM;             // one X atom: hi rows, then lo rows
+constexpr int OFF_RHI = 0;                 // R_off as the B operand: rows j, K = i
+constexpr int OFF_RLO = OFF_RHI + 4 * ATOM;
+constexpr int OFF_X = OFF_RLO + 4 * ATOM;  // two X atom slots
+constexpr int OFF_SELF = OFF_X + 2 * SLOT;         // 128 x float4 (A_hi, A_lo, B_hi, B_lo)
+constexpr int OFF_COEF = OFF_SELF + 4 * 128 * 4;   // 128 floats
+constexpr int OFF_DENS = OFF_COEF + 128 * 4;       // [4 quadrants][32] x (s, c)
+constexpr int OFF_BAR = OFF_DENS + 4 * 32 * 8;
+// barriers: full[2], empty[2], accf, acce, fin; then tmem slot, abort flag
+constexpr int NBAR = 7;
+constexpr int OFF_MISC = OFF_BAR + NBAR * 8;
+constexpr int SMEM_BYTES = OFF_MISC + 16 + 1024;  // + alignment slack
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t COL_HH1 = 128, COL_X = 256;   // accumulators: hh0 at 0, hh1, cross terms
+constexpr uint32_t COL_OFF = 384;                // epilogue copy of the summed accumulators
+constexpr uint32_t IDESC = tc::idesc_tf32(128, 128);
+
+static_assert(SMEM_BYTES <= 232448, "tensor-core rotation exceeds the shared-memory opt-in limit");
+
+__device__ unsigned int g_rotate_tc_aborts = 0;
+
+__device__ __forceinline__ void f2_add(float& s, float& c, float b, float extra) {
+  const float t = s + b;
+  const float bp = t - s;
+  c += ((s - (t - bp)) + (b - bp)) + extra;
+  s = t;
+}
+
+// lowbias32 integer mixer (C. Wellons, hash-prospector): counter-based
+// uniform bits for the dithered rounding of the self term.
+__device__ __forceinline__ unsigned mix32(unsigned x) {
+  x ^= x >> 16;
+  x *= 0x7feb352dU;
+  x ^= x >> 15;
+  x *= 0x846ca68bU;
+  x ^= x >> 16;
+  return x;
+}
+__device__ __forceinline__ void named_bar(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// uniform offset in (-ulp/2, ulp/2) of x from one byte
+__device__ __forceinline__ float dither(float x, unsigned byte) {
+  const float ulp = __uint_as_float(__float_as_uint(x) & 0x7f800000u) * 1.1920928955078125e-7f;
+  return ((float)byte * (1.0f / 256.0f) - 0.498046875f) * ulp;
+}
+
+__global__ void __launch_bounds__(NTHR, 1) k_rotate_tc(RotArgs<float> a, i64 ntiles) {
+  extern __shared__ unsigned char smem_raw[];
+  if (a.st && a.st->done) return;
+  if (!gate_open(a.st, a.gate)) return;
+
+  const uint32_t raw_addr = tc::smem_u32(smem_raw);
+  const uint32_t pad = (1024u - (raw_addr & 1023u)) & 1023u;
+  unsigned char* smem = smem_raw + pad;
+  const uint32_t sbase = raw_addr + pad;
+  float4* self = reinterpret_cast<float4*>(smem + OFF_SELF);  // (A_hi, A_lo, B_hi, B_lo) per orbital
+  float2* dens = reinterpret_cast<float2*>(smem + OFF_DENS);
+  float* coefs = reinterpret_cast<float*>(smem + OFF_COEF);
+  const uint32_t bar0 = sbase + OFF_BAR;
+  auto full_bar = [&](int k) { return bar0 + 8u * k; };
+  auto empty_bar = [&](int k) { return bar0 + 8u * (2 + k); };
+  const uint32_t accf_bar = bar0 + 32u, acce_bar = bar0 + 40u, fin_bar = bar0 + 48u;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + OFF_MISC);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + OFF_MISC + 4);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int N = a.N;
+  const i64 ng = a.ng;
+
+  // sources and destinations of the mode (see RotArgs)
+  int cur = 0;
+  const float* Wsrc;
+  const float* Hsrc = nullptr;
+  float* out;
+  double* rho;
+  double tau = 0.0;
+  if (a.trial) {
+    cur = a.st->cur;
+    Wsrc = a.W[cur];
+    Hsrc = a.HW[cur];
+    out = a.Wout[1 - cur];
+    rho = a.rho[1 - cur];
+    tau = a.st->tau_trial;
+  } else if (a.st) {
+    cur = a.st->cur;
+    if (a.src_cur_slot) {
+      Wsrc = a.Wout[cur];
+      out = a.Wout[cur];
+      rho = nullptr;  // a rotation within the span leaves rho unchanged
+    } else {
+      Wsrc = a.src_trial_slot ? a.Wout[1 - cur] : a.A;
+      out = a.Wout[1 - cur];
+      rho = a.rho[1 - cur];
+    }
+  } else {
+    Wsrc = a.A;
+    out = a.B;
+    rho = a.rho_out;
+  }
+  const float tauF = (float)tau;
+
+  // B operand = off-diagonal R (row j, K index i) split into TF32 pairs, the
+  // self-term coefficients, and the trial coefficients 1 + tau sigma_i
+  for (int idx = tid; idx < 128 * 128; idx += NTHR) {
+    const int i = idx >> 7, j = idx & 127;
+    double v = 0.0;
+    if (i < N && j < N && i != j && (a.general || i < j)) v = a.Rinv[(i64)i * N + j];
+    const float hi = tc::to_tf32((float)v);
+    const float lo = tc::to_tf32((float)(v - (double)hi));
+    const int off = (i >> 5) * ATOM + j * 128 + ((((i & 31) >> 2) ^ (j & 7)) << 4) + (i & 3) * 4;
+    *reinterpret_cast<float*>(smem + OFF_RHI + off) = hi;
+    *reinterpret_cast<float*>(smem + OFF_RLO + off) = lo;
+  }
+  for (int j = tid; j < 128; j += NTHR) {
+    double A = 0.0, B = 0.0, cf = 1.0;
+    if (j < N) {
+      const double v = a.Rinv[(i64)j * N + j];
+      A = v;
+      if (a.trial) {
+        cf = 1.0 + tau * a.sigma[cur][j];
+        A = v * cf;
+        B = v * tau;
+      }
+    }
+    const float ah = (float)A, bh = (float)B;
+    self[j] = make_float4(ah, (float)(A - (double)ah), bh, (float)(B - (double)bh));
+    coefs[j] = (float)cf;
+  }
+  if (tid == 0) {
+    for (int k = 0; k < 2; ++k) {
+      tc::mbar_init(full_bar(k), PROD_WARPS * 32);
+      tc::mbar_init(empty_bar(k), 1);
+    }
+    tc::mbar_init(accf_bar, 1);
+    tc::mbar_init(acce_bar, EPI_WARPS * 32);
+    tc::mbar_init(fin_bar, 1);
+    *abort_flag = 0;
+    tc::mbar_init_fence();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tc::smem_u32(tmem_slot), TMEM_COLS);
+    tc::tmem_relinquish();
+  }
+  tc::fence_proxy_async_smem();  // R tiles written by the generic proxy
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  const i64 G = gridDim.x;
+  const i64 t0 = ntiles * (i64)blockIdx.x / G, t1 = ntiles * (i64)(blockIdx.x + 1) / G;
+  const int nmine = (int)(t1 - t0);
+  const int natoms = 4 * nmine;
+  const bool vec4 = (ng % 4 == 0) && ((reinterpret_cast<uintptr_t>(Wsrc) & 15u) == 0) &&
+                    (Hsrc == nullptr || (reinterpret_cast<uintptr_t>(Hsrc) & 15u) == 0);
+
+  if (warp < PROD_WARPS) {
+    // ------------------------------------------------------------ producers
+    // Atom u = 4 t + k of this CTA (tile t, orbitals 32 k .. 32 k + 31) goes
+    // to slot u & 1.  Thread (warp w, lane l) owns orbital 32 k + 4 w + l / 8
+    // and the four points 4 q .. 4 q + 3 (q = l % 8) of each 32-point group g.
+    const int q = lane & 7, isub = lane >> 3;
+    auto issue = [&](int u, float4 (&wv)[4], float4 (&hv)[4]) {
+      const int k = u & 3;
+      const i64 p0 = (t0 + (u >> 2)) * TPTS + 4 * q;
+      const int i = 32 * k + 4 * warp + isub;
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        wv[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+        hv[g] = wv[g];
+      }
+      if (i >= N) return;
+      const i64 base = (i64)i * ng + p0;
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        const i64 p = p0 + 32 * g;
+        if (vec4) {
+          if (p < ng) {  // ng % 4 == 0: a chunk is wholly inside the row or past it
+            wv[g] = __ldg(reinterpret_cast<const float4*>(Wsrc + base + 32 * g));
+            if (Hsrc) hv[g] = __ldg(reinterpret_cast<const float4*>(Hsrc + base + 32 * g));
+          }
+        } else {
+          float w1[4] = {0.f, 0.f, 0.f, 0.f}, h1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (p + e < ng) {
+              w1[e] = Wsrc[base + 32 * g + e];
+              if (Hsrc) h1[e] = Hsrc[base + 32 * g + e];
+            }
+          wv[g] = make_float4(w1[0], w1[1], w1[2], w1[3]);
+          hv[g] = make_float4(h1[0], h1[1], h1[2], h1[3]);
+        }
+      }
+    };
+    bool issued = false;
+    // one atom: loads for atom u + 2 go into the register set that held
+    // atom u - 1; atom u is written from (w, h)
+    auto step = [&](int u, const float4 (&w)[4], const float4 (&h)[4], float4 (&wl)[4], float4 (&hl)[4]) -> bool {
+      if (u + 2 < natoms) issue(u + 2, wl, hl);
+      const int k = u & 3, slot = u & 1, n = u >> 1;
+      if (n > 0 && !tc::mbar_wait(empty_bar(slot), (n - 1) & 1, abort_flag)) return false;
+      unsigned char* xs = smem + OFF_X + slot * SLOT;
+      const float cf = coefs[32 * k + 4 * warp + isub];
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        float x[4] = {w[g].x, w[g].y, w[g].z, w[g].w};
+        if (Hsrc) {
+          const float h4[4] = {h[g].x, h[g].y, h[g].z, h[g].w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) x[e] = cf * x[e] - tauF * h4[e];
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int row = 32 * g + 8 * e + q;  // holds point 32 g + 4 q + e; row % 8 == q
+          const float hi = tc::to_tf32(x[e]);
+          const float lo = tc::to_tf32(x[e] - hi);
+          const int off = row * 128 + ((warp ^ q) << 4) + isub * 4;
+          *reinterpret_cast<float*>(xs + off) = hi;
+          *reinterpret_cast<float*>(xs + ATOM + off) = lo;
+        }
+      }
+      tc::fence_proxy_async_smem();
+      tc::mbar_arrive(full_bar(slot));
+      if (warp == 0) {
+        // ---------------------------------------------------- MMA issue
+        int ok = 1;
+        if (lane == 0) {
+          const int t = u >> 2;
+          if (k == 0 && t > 0) ok = tc::mbar_wait(acce_bar, (t - 1) & 1, abort_flag);
+          if (ok) ok = tc::mbar_wait(full_bar(slot), n & 1, abort_flag);
+          if (ok) {
+            tc::fence_after_sync();
+            const uint32_t xh = sbase + OFF_X + slot * SLOT, xl = xh + ATOM;
+            const uint32_t rh = sbase + OFF_RHI + k * ATOM, rl = sbase + OFF_RLO + k * ATOM;
+            const uint32_t dhh = tmem + ((k >> 1) ? COL_HH1 : 0u), dx = tmem + COL_X;
+#pragma unroll
+            for (int s4 = 0; s4 < 4; ++s4) {
+              const uint64_t axh = tc::desc_sw128(xh + 32u * s4), axl = tc::desc_sw128(xl + 32u * s4);
+              const uint64_t brh = tc::desc_sw128(rh + 32u * s4), brl = tc::desc_sw128(rl + 32u * s4);
+              tc::mma_tf32(dhh, axh, brh, IDESC, ((k & 1) == 0 && s4 == 0) ? 0u : 1u);
+              tc::mma_tf32(dx, axh, brl, IDESC, (k == 0 && s4 == 0) ? 0u : 1u);
+              tc::mma_tf32(dx, axl, brh, IDESC, 1u);
+            }
+            issued = true;
+            tc::mma_commit(empty_bar(slot));
+            if (k == 3) tc::mma_commit(accf_bar);
+          }
+        }
+        if (!__shfl_sync(0xffffffffu, ok, 0)) return false;
+      }
+      return true;
+    };
+    float4 wA[4], hA[4], wB[4], hB[4], wC[4], hC[4];
+    if (natoms > 0) issue(0, wA, hA);
+    if (natoms > 1) issue(1, wB, hB);
+    for (int u = 0; u < natoms; u += 3) {
+      if (!step(u, wA, hA, wC, hC)) break;
+      if (u + 1 >= natoms || !step(u + 1, wB, hB, wA, hA)) break;
+      if (u + 2 >= natoms || !step(u + 2, wC, hC, wB, hB)) break;
+    }
+    if (warp == 0 && lane == 0 && issued) {
+      // every MMA issued has completed before tensor memory is released
+      tc::mma_commit(fin_bar);
+      tc::mbar_wait(fin_bar, 0, abort_flag, 4000000000ull);
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int quad = warp & 3;              // TMEM lane quadrant: tile points 32 quad .. 32 quad + 31
+    const int jh = (warp - EPI0) >> 2;      // output columns 64 jh .. 64 jh + 63
+    const int pt = 32 * quad + 4 * (lane & 7) + (lane >> 3);  // tile point of this thread's lane
+    const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
+    const uint32_t off_col = COL_OFF + (uint32_t)(64 * jh);  // this warp's copy of its 64 sums
+    const unsigned seed32 = mix32((unsigned)(a.st ? a.st->passes : 0) * 4u + (unsigned)a.sr_salt + 0x85ebca6bu);
+    // w and hw of one 8-column group for this lane's point
+    auto fetch = [&](i64 p, int g, float (&wv)[8], float (&hv)[8]) {
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int j = 64 * jh + 8 * g + m;
+        wv[m] = hv[m] = 0.f;
+        if (p < ng && j < N) {
+          wv[m] = Wsrc[(i64)j * ng + p];
+          if (Hsrc) hv[m] = Hsrc[(i64)j * ng + p];
+        }
+      }
+    };
+    // density of this lane's point over the 64 columns: four independent
+    // double-float chains (one per column mod 4), so that the compensated
+    // additions do not form one serial dependency
+    float rs[4], rc[4];
+    // one 8-column group: self term, dithered rounding, store, squares
+    auto finish = [&](i64 p, int g, const float (&wv)[8], const float (&hv)[8]) {
+      uint32_t ov[8];
+      tc::tmem_ld8(lane_base + off_col + (uint32_t)(8 * g), ov);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int m4 = 0; m4 < 8; m4 += 4) {
+        // one 32-bit draw per (4 columns, point): one byte per element
+        const unsigned bits =
+            mix32(seed32 ^ mix32((unsigned)((64 * jh + 8 * g + m4) >> 2) * 0x9e3779b1u ^ (unsigned)p));
+#pragma unroll
+        for (int m = m4; m < m4 + 4; ++m) {
+          const int j = 64 * jh + 8 * g + m;
+          const float4 c = self[j];  // A_hi, A_lo, B_hi, B_lo
+          const float d = dither(wv[m], (bits >> (8 * (m - m4))) & 0xffu);
+          const float rest = fmaf(c.y, wv[m], fmaf(-c.w, hv[m], __uint_as_float(ov[m]) + d));
+          const float o = fmaf(c.x, wv[m], fmaf(-c.z, hv[m], rest));
+          if (p < ng && j < N) {
+            out[(i64)j * ng + p] = o;
+            const float sq = o * o;
+            f2_add(rs[m - m4], rc[m - m4], sq, fmaf(o, o, -sq));
+          }
+        }
+      }
+    };
+    float wA[8], hA[8], wB[8], hB[8];
+    if (nmine > 0) fetch(t0 * TPTS + pt, 0, wA, hA);
+    for (int t = 0; t < nmine; ++t) {
+      const i64 p = (t0 + t) * TPTS + pt;
+      if (!tc::mbar_wait(accf_bar, t & 1, abort_flag)) break;
+      tc::fence_after_sync();
+      // off-diagonal sums: the three accumulators added and copied to this
+      // warp's free tensor-memory columns, then released
+#pragma unroll 1
+      for (int c = 0; c < 64; c += 16) {
+        uint32_t h0[16], h1[16], xx[16];
+        tc::tmem_ld16(lane_base + (uint32_t)(64 * jh + c), h0);
+        tc::tmem_ld16(lane_base + COL_HH1 + (uint32_t)(64 * jh + c), h1);
+        tc::tmem_ld16(lane_base + COL_X + (uint32_t)(64 * jh + c), xx);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int m = 0; m < 16; ++m)
+          h0[m] = __float_as_uint((__uint_as_float(h0[m]) + __uint_as_float(h1[m])) + __uint_as_float(xx[m]));
+        tc::tmem_st16(lane_base + off_col + (uint32_t)c, h0);
+      }
+      tc::tmem_wait_st();
+      tc::fence_before_sync();
+      tc::mbar_arrive(acce_bar);  // accumulators free: the next tile's MMAs may start
+
+#pragma unroll
+      for (int c = 0; c < 4; ++c) rs[c] = rc[c] = 0.f;
+      // groups 0..7, the next group's loads in flight while one is finished
+#pragma unroll 1
+      for (int g = 0; g < 8; g += 2) {
+        fetch(p, g + 1, wB, hB);
+        finish(p, g, wA, hA);
+        if (g + 2 < 8)
+          fetch(p, g + 2, wA, hA);
+        else if (t + 1 < nmine)
+          fetch(p + TPTS, 0, wA, hA);
+        finish(p, g + 1, wB, hB);
+      }
+      f2_add(rs[0], rc[0], rs[1], rc[1]);
+      f2_add(rs[2], rc[2], rs[3], rc[3]);
+      f2_add(rs[0], rc[0], rs[2], rc[2]);
+      if (rho != nullptr) {
+        // the two warps of this quadrant hold the two column halves
+        float2* dq = dens + quad * 32;
+        if (jh == 1) dq[lane] = make_float2(rs[0], rc[0]);
+        named_bar(1 + quad, 64);
+        if (jh == 0 && p < ng) {
+          const float2 o2 = dq[lane];
+          rho[p] = F_OCC * (((double)rs[0] + (double)rc[0]) + ((double)o2.x + (double)o2.y));
+        }
+        named_bar(1 + quad, 64);
+      }
+    }
+  }
+
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, TMEM_COLS);
+  }
+  if (*abort_flag != 0 && tid == 0) {
+    atomicAdd(&g_rotate_tc_aborts, 1u);
+    if (a.st) {
+      State* w = const_cast<State*>(a.st);
+      w->status = 3;  // POU_ECUDA: a pipeline wait gave up
+      w->done = 1;
+    }
+  }
+}
+
+bool g_configured = false;
+
+}  // namespace
+
+int rotate_tc_grid(i64 ng) {
+  const i64 ntiles = (ng + TPTS - 1) / TPTS;
+  return (int)std::max<i64>(1, std::min<i64>(152, ntiles));
+}
+
+void configure_rotate_tc() {
+  if (g_configured) return;
+  cudaFuncSetAttribute(k_rotate_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  g_configured = true;
+}
+
+void launch_rotate_tc(const RotArgs<float>& a, cudaStream_t s) {
+  configure_rotate_tc();
+  const i64 ntiles = (a.ng + TPTS - 1) / TPTS;
+  prof_begin("rotate_density", s);
+  k_rotate_tc<<<rotate_tc_grid(a.ng), NTHR, SMEM_BYTES, s>>>(a, ntiles);
+  prof_end(s);
+}
+
+}  // namespace pou

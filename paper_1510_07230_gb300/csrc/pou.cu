@@ -116,8 +116,6 @@ struct pou_ctx {
   double* Rinv;
   double* split;
   size_t split_elems;
-  double* normpart;  // column norms written by the rotation (FP32 form)
-  int nnorm;
   double* evec;      // eigenvector scratch of the subspace diagonalisation
   void* dv;          // V(trial) - V(current), working type (written by the potential pass)
   State* st;
@@ -265,8 +263,6 @@ void enqueue_second_orth(pou_ctx* c) {
   r.dV = c->dV;
   r.S = c->S;
   r.gate = 1;
-  r.normpart = c->normpart;
-  r.nnorm = c->nnorm;
   launch_gram_reduce(r, s);
   launch_cholinv(c->st, c->S, c->Rinv, c->N, nullptr, c->st, pivot_tol(c), -1.0, s);
   RotArgs<T> ra{};
@@ -419,7 +415,6 @@ void enqueue_pass(pou_ctx* c) {
   }
   ra.Rinv = c->Rinv;
   ra.trial = 1;
-  ra.normpart = c->dt == 1 ? c->normpart : nullptr;
   ra.ng = c->ng;
   ra.N = c->N;
   launch_rotate<T>(ra, s);
@@ -527,7 +522,6 @@ pou_status init_from_staged(pou_ctx* c) {
   ra.A = tp<T>(c->W[0]);
   ra.Rinv = c->Rinv;
   ra.trial = 0;
-  ra.normpart = c->dt == 1 ? c->normpart : nullptr;
   ra.ng = c->ng;
   ra.N = c->N;
   launch_rotate<T>(ra, s);
@@ -795,6 +789,7 @@ void pou::configure_kernels() {
   configure_eigh();
   configure_apply_h();
   configure_gram_tc();
+  configure_rotate_tc();
   done = true;
 }
 
@@ -920,8 +915,6 @@ static pou_status create_buffers(pou_ctx* c) {
     c->split_elems = (size_t)nsplit * npair * ST * ST;
     DALLOC(c->split, c->split_elems * sizeof(double));
   }
-  c->nnorm = 2 * rotate_grid(c->ng, (int)c->esz);
-  DALLOC(c->normpart, (size_t)c->nnorm * c->N * sizeof(double));
   DALLOC(c->evec, (size_t)c->N * c->N * sizeof(double));
   DALLOC(c->dv, c->ng * c->esz);
   DALLOC(c->st, sizeof(State));
@@ -941,7 +934,7 @@ void pou_destroy(pou_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   void* ptrs[] = {c->W[0], c->W[1], c->HW[0], c->HW[1], c->V[0], c->V[1], c->rho[0], c->rho[1],
                   c->sigma[0], c->sigma[1], c->part[0], c->part[1], c->vext, c->work, c->tilepart,
-                  c->epart, c->S, c->Rinv, c->split, c->normpart, c->evec, c->dv, c->st, c->hist_E, c->hist_tau, c->info,
+                  c->epart, c->S, c->Rinv, c->split, c->evec, c->dv, c->st, c->hist_E, c->hist_tau, c->info,
                   c->dR, c->dZ, c->tabs.gx, c->fpart, c->ublock, c->gblock, c->rho_e, c->V64_e};
   for (void* p : ptrs)
     if (p) cudaFree(p);

@@ -131,8 +131,6 @@ struct GramReduceArgs {
   const double* part[2];
   int fp32_coef;        // coefficients rounded to FP32 as in the FP32 kernels
   int gate;             // see gate_open
-  const double* normpart;  // diagonal from exact column norms: [nnorm][N] raw sums
-  int nnorm;
 };
 void launch_gram_reduce(const GramReduceArgs& a, cudaStream_t s);
 
@@ -152,13 +150,17 @@ struct RotArgs {
   int src_trial_slot;   // plain mode with state: source W[1-cur], written in place
   int src_cur_slot;     // plain mode with state: source W[cur], written in place (W <- W P)
   int gate;             // see gate_open
-  double* normpart;     // [2 * gridDim][N] raw column norms of the output (nullable)
   int sr_salt;          // distinguishes the rotations of one pass in the rounding counter
   i64 ng;
   int N;
   int general;          // 1: full matrix (no triangular skip)
 };
 int rotate_grid(i64 ng, int elem_bytes);
+// FP32 rotation on the tensor cores (TF32 split products for the
+// off-diagonal part), N <= 128; one CTA per SM.
+int rotate_tc_grid(i64 ng);
+void launch_rotate_tc(const RotArgs<float>& a, cudaStream_t s);
+void configure_rotate_tc();
 template <typename T>
 void launch_rotate(const RotArgs<T>& a, cudaStream_t s);
 
