@@ -470,7 +470,7 @@ void launch_gram(const GramArgs<T>& a, cudaStream_t s) {
   }
   const int nsup = (a.N + GT<T>::ST - 1) / GT<T>::ST;
   dim3 grid(nsplit, npair);
-  prof_begin("gram", s);
+  prof_begin(gram_prof_name(a.trial, a.src_trial_slot, a.src_cur_pair), s);
   k_gram<T><<<grid, GNT, 0, s>>>(a, ntiles, nsup, npair);
   prof_end(s);
 }
@@ -490,7 +490,7 @@ void launch_gram_nsplit(const GramArgs<T>& a, int nsplit, cudaStream_t s) {
   }
   const int nsup = (a.N + GT<T>::ST - 1) / GT<T>::ST;
   dim3 grid(nsplit, npair);
-  prof_begin("gram", s);
+  prof_begin(gram_prof_name(a.trial, a.src_trial_slot, a.src_cur_pair), s);
   k_gram<T><<<grid, GNT, 0, s>>>(a, ntiles, nsup, npair);
   prof_end(s);
 }
@@ -526,7 +526,7 @@ void launch_rotate(const RotArgs<T>& a, cudaStream_t s) {
     launch_rotate_tc(a, s);
   } else {
     const int nchunks = (int)((a.ng + RP - 1) / RP);
-    prof_begin("rotate_density", s);
+    prof_begin(rotate_prof_name(a.trial, a.src_trial_slot, a.src_cur_slot), s);
     k_rotate<<<rotate_grid(a.ng, 8), RNT, rotate_smem(), s>>>(a, nchunks);
     prof_end(s);
   }

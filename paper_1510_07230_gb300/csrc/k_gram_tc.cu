@@ -365,7 +365,7 @@ void configure_gram_tc() {
 void launch_gram_tc(const GramArgs<float>& a, int nsplit, cudaStream_t s) {
   configure_gram_tc();
   const i64 nkb = (a.ng + KB - 1) / KB;
-  prof_begin("gram", s);
+  prof_begin(gram_prof_name(a.trial, a.src_trial_slot, a.src_cur_pair), s);
   // one split per CTA; a CTA without stages writes zeros
   // the source rows of the mode: W[cur] and HW[cur] (trial), W[1 - cur], or A
   bool vec = (a.ng % 4) == 0;

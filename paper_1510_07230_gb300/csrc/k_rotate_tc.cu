@@ -460,7 +460,7 @@ void configure_rotate_tc() {
 void launch_rotate_tc(const RotArgs<float>& a, cudaStream_t s) {
   configure_rotate_tc();
   const i64 ntiles = (a.ng + TPTS - 1) / TPTS;
-  prof_begin("rotate_density", s);
+  prof_begin(rotate_prof_name(a.trial, a.src_trial_slot, a.src_cur_slot), s);
   k_rotate_tc<<<rotate_tc_grid(a.ng), NTHR, SMEM_BYTES, s>>>(a, ntiles);
   prof_end(s);
 }

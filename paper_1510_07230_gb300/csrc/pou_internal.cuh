@@ -256,6 +256,18 @@ void configure_kernels();
 void launch_eigh(const State* st, const double* Sig, double* P, double* VT, double* ev0, double* ev1, int N,
                  cudaStream_t s);
 
+// Profiler names of the Gram and rotation launches by source: the trial
+// block (2 blocks read by the Gram, 2 read + 1 written by the rotation), the
+// second Cholesky-QR pass on the block just written (1; 1 + 1), the subspace
+// pair of Algorithm M, or a caller's block.
+inline const char* gram_prof_name(int trial, int src_trial_slot, int src_cur_pair) {
+  return trial ? "gram" : src_trial_slot ? "gram_reorth" : src_cur_pair ? "gram_sigma" : "gram_plain";
+}
+inline const char* rotate_prof_name(int trial, int src_trial_slot, int src_cur_slot) {
+  return trial ? "rotate_density" : src_trial_slot ? "rotate_reorth" : src_cur_slot ? "rotate_subspace"
+                                                                                    : "rotate_plain";
+}
+
 // Counts every kernel launched by the library (host side).
 extern long long g_launches;
 
