@@ -117,6 +117,9 @@ typedef struct {
   double df_mean3;       /* (df^l + df^(l-1) + df^(l-2)) / 3 of Sec. 4.2 */
   double grad_norm;      /* ||HW - W Sigma||_F (Eq. gra) when computed, else -1 */
   double gram_offdiag;   /* max |S - I| of the last accepted trial Gram matrix */
+  int second_passes;     /* FP32 form: trials orthonormalised twice by this call (Cholesky-QR
+                            repeated when max |S - I| > 0.02); 0 in the FP64 form */
+  int diagonalisations;  /* subspace diagonalisations (Algorithm M) by this call */
 } pou_report;
 
 /* Fill a config with the paper's constants (Sec. 3.2) and FP64 defaults. */

@@ -1093,6 +1093,8 @@ pou_status pou_iterate(pou_ctx* c, int max_iter, double e_tol, double grad_tol, 
     rep->df_mean3 = hs.n_df >= 3 ? (hs.df[0] + hs.df[1] + hs.df[2]) / 3.0 : -1.0;
     rep->grad_norm = grad;
     rep->gram_offdiag = hs.gram_off_acc;
+    rep->second_passes = hs.reorth_count - start.reorth_count;
+    rep->diagonalisations = hs.diag_count - start.diag_count;
   }
   if (hs.status == POU_ENOTSPD)
     return fail(c, POU_ENOTSPD, "trial Gram matrix not positive definite (pivot %d)", hs.chol_info);

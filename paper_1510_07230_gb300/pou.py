@@ -57,7 +57,7 @@ class Report(C.Structure):
     _fields_ = [("iterations", C.c_int), ("passes", C.c_int), ("backtracks", C.c_int), ("forced", C.c_int),
                 ("total_iterations", C.c_int), ("converged", C.c_int), ("energy", C.c_double),
                 ("tau", C.c_double), ("df_mean3", C.c_double), ("grad_norm", C.c_double),
-                ("gram_offdiag", C.c_double)]
+                ("gram_offdiag", C.c_double), ("second_passes", C.c_int), ("diagonalisations", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
