@@ -384,6 +384,154 @@ __global__ void __launch_bounds__(RNT) k_rotate(RotArgs<double> a, int nchunks) 
   }
 }
 
+// FP32 form, general rotation W <- W P of Algorithm M (P dense, far from the
+// identity) on the CUDA cores.  There every output is an O(1) mixture of the
+// inputs, and the tensor-core path (TF32 split products, truncating FP32
+// accumulation) would leave errors of a few 1e-7 relative in the rotated
+// orbitals; here every product is an exact FP32 FMA with round-to-nearest
+// accumulation, and the self term P_jj w_j is added with double-float
+// coefficients and stored with unbiased (dithered) rounding like the
+// tensor-core rotation.  Runs once every n_diag steps.
+__device__ __forceinline__ unsigned mix32(unsigned x) {
+  // lowbias32 integer mixer (C. Wellons, hash-prospector)
+  x ^= x >> 16;
+  x *= 0x7feb352dU;
+  x ^= x >> 15;
+  x *= 0x846ca68bU;
+  x ^= x >> 16;
+  return x;
+}
+__device__ __forceinline__ float dither(float x, unsigned byte) {
+  const float ulp = __uint_as_float(__float_as_uint(x) & 0x7f800000u) * 1.1920928955078125e-7f;
+  return ((float)byte * (1.0f / 256.0f) - 0.498046875f) * ulp;
+}
+
+__global__ void __launch_bounds__(RNT) k_rotate_f32_cc(RotArgs<float> a, int nchunks) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = a.N;
+  const int NPAD = 128;
+  float* Rs = reinterpret_cast<float*>(smem_raw);  // [NPAD][NPAD], zero diagonal
+  float* Xs = Rs + NPAD * NPAD;                     // [NPAD][RP + 4]
+  float* self = Xs + NPAD * (RP + 4);               // [2][NPAD]: P_jj hi, lo
+  constexpr int XS = RP + 4;
+
+  if (a.st && a.st->done) return;
+  if (!gate_open(a.st, a.gate)) return;
+  const int tid = threadIdx.x;
+  const float* Wsrc;
+  float* out;
+  double* rho;
+  if (a.st) {
+    const int cur = a.st->cur;
+    if (a.src_cur_slot) {
+      Wsrc = a.Wout[cur];
+      out = a.Wout[cur];
+      rho = nullptr;  // a rotation within the span leaves rho unchanged
+    } else {
+      Wsrc = a.src_trial_slot ? a.Wout[1 - cur] : a.A;
+      out = a.Wout[1 - cur];
+      rho = a.rho[1 - cur];
+    }
+  } else {
+    Wsrc = a.A;
+    out = a.B;
+    rho = a.rho_out;
+  }
+  for (int idx = tid; idx < NPAD * NPAD; idx += RNT) {
+    const int i = idx / NPAD, j = idx % NPAD;
+    const double v = (i < N && j < N && (a.general || i <= j)) ? a.Rinv[(i64)i * N + j] : 0.0;
+    Rs[idx] = (i == j) ? 0.f : (float)v;
+    if (i == j) {
+      self[i] = (float)v;
+      self[NPAD + i] = (float)(v - (double)(float)v);
+    }
+  }
+  __syncthreads();
+  const unsigned seed32 = mix32((unsigned)(a.st ? a.st->passes : 0) * 4u + (unsigned)a.sr_salt + 0x85ebca6bu);
+
+  const int lane = tid & 31, warp = tid >> 5;
+  const int jw = warp & 3, pw = warp >> 2;
+  const int jg = lane & 3, pg = lane >> 2;
+  const int j0 = jw * 32 + jg * 8;  // 8 output orbitals
+  const int pl0 = pw * 32 + pg * 4; // 4 points within the chunk
+  const int imax = a.general ? N : min(N, j0 + 8);
+  const i64 ng = a.ng;
+
+  for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const i64 p0 = (i64)ch * RP;
+    for (int idx = tid; idx < N * RP; idx += RNT) {
+      const int i = idx / RP, pp = idx % RP;
+      const i64 gp = p0 + pp;
+      Xs[i * XS + pp] = gp < ng ? Wsrc[(i64)i * ng + gp] : 0.f;
+    }
+    __syncthreads();
+
+    float acc[8][4];
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[jj][q] = 0.f;
+    for (int i = 0; i < imax; ++i) {
+      float rv[8], xv[4];
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) rv[jj] = Rs[i * NPAD + j0 + jj];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) xv[q] = Xs[i * XS + pl0 + q];
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[jj][q] = fmaf(rv[jj], xv[q], acc[jj][q]);
+    }
+    // self term with double-float P_jj, unbiased rounding; density in double-float
+    float ds[4] = {0.f, 0.f, 0.f, 0.f}, dc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+      const int j = j0 + jj;
+      if (j >= N) continue;
+      const float ph = self[j], plo = self[NPAD + j];
+      const unsigned bits = mix32(seed32 ^ mix32((unsigned)j * 0x9e3779b1u ^ (unsigned)(p0 + pl0)));
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float wv = Xs[j * XS + pl0 + q];
+        const float d = dither(wv, (bits >> (8 * q)) & 0xffu);
+        const float o = fmaf(ph, wv, fmaf(plo, wv, acc[jj][q] + d));
+        const i64 gp = p0 + pl0 + q;
+        if (gp < ng) out[(i64)j * ng + gp] = o;
+        const float sq = o * o;
+        F2 f{ds[q], dc[q]};
+        two_sum_add(f, sq, fmaf(o, o, -sq));
+        ds[q] = f.s;
+        dc[q] = f.c;
+      }
+    }
+    if (rho != nullptr) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        for (int o = 1; o <= 2; o <<= 1) {
+          F2 f{ds[q], dc[q]};
+          two_sum_add(f, __shfl_xor_sync(0xffffffffu, ds[q], o), __shfl_xor_sync(0xffffffffu, dc[q], o));
+          ds[q] = f.s;
+          dc[q] = f.c;
+        }
+      }
+    }
+    __syncthreads();  // Xs no longer read; reuse a region for the density
+    if (rho != nullptr) {
+      double* dsum = reinterpret_cast<double*>(Xs);  // [4][RP]
+      if (jg == 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dsum[jw * RP + pl0 + q] = (double)ds[q] + (double)dc[q];
+      }
+      __syncthreads();
+      if (tid < RP) {
+        const i64 gp = p0 + tid;
+        if (gp < ng) rho[gp] = F_OCC * (dsum[tid] + dsum[RP + tid] + dsum[2 * RP + tid] + dsum[3 * RP + tid]);
+      }
+      __syncthreads();
+    }
+  }
+}
+
 template <typename T>
 __global__ void k_density(const T* U, i64 ng, int N, double* rho) {
   const i64 p = (i64)blockIdx.x * blockDim.x + threadIdx.x;
@@ -509,9 +657,14 @@ static size_t rotate_smem() {
   const int NPAD = 128;
   return sizeof(double) * ((size_t)NPAD * NPAD + (size_t)NPAD * (RP + 4) + NPAD);
 }
+static size_t rotate_f32_smem() {
+  const int NPAD = 128;
+  return sizeof(float) * ((size_t)NPAD * NPAD + (size_t)NPAD * (RP + 4) + 2 * NPAD);
+}
 
 void configure_rotate() {
   cudaFuncSetAttribute(k_rotate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rotate_smem());
+  cudaFuncSetAttribute(k_rotate_f32_cc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rotate_f32_smem());
 }
 
 int rotate_grid(i64 ng, int elem_bytes) {
@@ -523,7 +676,15 @@ int rotate_grid(i64 ng, int elem_bytes) {
 template <typename T>
 void launch_rotate(const RotArgs<T>& a, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
-    launch_rotate_tc(a, s);
+    if (a.general && !a.trial) {
+      // dense P of Algorithm M: CUDA cores, exact FP32 products
+      const int nchunks = (int)((a.ng + RP - 1) / RP);
+      prof_begin(rotate_prof_name(a.trial, a.src_trial_slot, a.src_cur_slot), s);
+      k_rotate_f32_cc<<<std::min(nchunks, 2 * 152), RNT, rotate_f32_smem(), s>>>(a, nchunks);
+      prof_end(s);
+    } else {
+      launch_rotate_tc(a, s);
+    }
   } else {
     const int nchunks = (int)((a.ng + RP - 1) / RP);
     prof_begin(rotate_prof_name(a.trial, a.src_trial_slot, a.src_cur_slot), s);
