@@ -4,6 +4,15 @@
 // (status POU_ENOTSPD, done = 1); no trap, no wait.
 // The same kernel records max |S - I| of the trial Gram matrix, the
 // near-identity diagnostic of Fig. 2.
+//
+// Blocked, 32-wide panels.  Factorisation (right-looking): the diagonal
+// block is factored by one warp with warp-level synchronisation only, the
+// panel row is solved column by column in parallel, and the trailing matrix
+// is updated with 4 x 4 register tiles (two FP64 FMAs per shared-memory
+// load).  Inverse X = R^-1: the diagonal blocks are inverted by one warp
+// each (one column per lane), then the off-diagonal blocks level by level,
+// X_pq = -X_pp sum_{r=p+1..q} R_pr X_rq, all blocks of a level at once.
+// X^T is kept in the (unused) lower triangle of the working matrix.
 #include "pou_internal.cuh"
 
 namespace pou {
@@ -11,18 +20,22 @@ namespace pou {
 namespace {
 
 constexpr int CNT = 512;
+constexpr int NB = 32;       // panel width
+constexpr int MAXB = 4;      // panels for N <= 128
 
 __global__ void __launch_bounds__(CNT) k_cholinv(const State* st_ro, State* st, const double* S,
                                                   double* Rinv, int N, int* info, double piv_rel,
                                                   double reorth_thr) {
-  extern __shared__ double A[];  // [N][N+1]
-  __shared__ int fail;
+  extern __shared__ double A[];  // [N][N+1]: upper = R, strictly lower = X^T
+  __shared__ double rdiag[128];  // 1 / R_ii
+  __shared__ double T[MAXB - 1][NB][NB + 1];  // sums of one level of the inverse
+  __shared__ volatile int fail;
   __shared__ double offmax[CNT / 32];
   __shared__ double dmax;
   if (st_ro && st_ro->done) return;
   if (reorth_thr < 0.0 && !(st_ro && st_ro->reorth)) return;  // gated second pass
   const int ld = N + 1;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   double om = 0.0;
   for (int idx = tid; idx < N * N; idx += CNT) {
     const int i = idx / N, j = idx % N;
@@ -31,7 +44,7 @@ __global__ void __launch_bounds__(CNT) k_cholinv(const State* st_ro, State* st, 
     om = fmax(om, fabs(v - (i == j ? 1.0 : 0.0)));
   }
   for (int o = 16; o > 0; o >>= 1) om = fmax(om, __shfl_xor_sync(0xffffffffu, om, o));
-  if ((tid & 31) == 0) offmax[tid >> 5] = om;
+  if (lane == 0) offmax[warp] = om;
   __syncthreads();
   if (tid == 0) {
     fail = 0;
@@ -50,27 +63,87 @@ __global__ void __launch_bounds__(CNT) k_cholinv(const State* st_ro, State* st, 
   }
   __syncthreads();
 
-  // right-looking factorisation, upper triangle holds R
-  for (int k = 0; k < N; ++k) {
-    if (tid == 0) {
-      const double d = A[k * ld + k];
-      // a pivot at rounding level of the largest diagonal entry means the
-      // columns are numerically dependent
-      if (!(d > piv_rel * dmax) || !isfinite(d)) {
-        fail = k + 1;
-      } else {
-        A[k * ld + k] = sqrt(d);
+  const int np = (N + NB - 1) / NB;
+  // ------------------------------------------------------------ factorisation
+  for (int p = 0; p < np; ++p) {
+    const int c0 = p * NB, c1 = min(N, c0 + NB);
+    if (warp == 0) {
+      // diagonal block, right-looking, lane = column c0 + lane
+      const int j = c0 + lane;
+      for (int k = c0; k < c1; ++k) {
+        if (lane == 0) {
+          const double d = A[k * ld + k];
+          // a pivot at rounding level of the largest diagonal entry means the
+          // columns are numerically dependent
+          if (!(d > piv_rel * dmax) || !isfinite(d)) {
+            fail = k + 1;
+          } else {
+            const double r = sqrt(d);
+            A[k * ld + k] = r;
+            rdiag[k] = 1.0 / r;
+          }
+        }
+        __syncwarp();
+        if (fail) break;
+        const double rk = rdiag[k];
+        if (j > k && j < c1) A[k * ld + j] *= rk;
+        __syncwarp();
+        if (j > k && j < c1) {
+          const double akj = A[k * ld + j];
+          for (int i = k + 1; i <= j; ++i) A[i * ld + j] -= A[k * ld + i] * akj;
+        }
+        __syncwarp();
       }
     }
     __syncthreads();
     if (fail) break;
-    const double rkk = A[k * ld + k];
-    for (int j = k + 1 + tid; j < N; j += CNT) A[k * ld + j] /= rkk;
+    // panel row: R[c0:c1, j] = R_pp^-T A[c0:c1, j] for j >= c1, one column per thread
+    for (int j = c1 + tid; j < N; j += CNT) {
+      for (int i = c0; i < c1; ++i) {
+        const double x = A[i * ld + j] * rdiag[i];
+        A[i * ld + j] = x;
+        for (int k = i + 1; k < c1; ++k) A[k * ld + j] -= A[i * ld + k] * x;
+      }
+    }
     __syncthreads();
-    const int m = N - k - 1;
-    for (int idx = tid; idx < m * m; idx += CNT) {
-      const int i = k + 1 + idx / m, j = k + 1 + idx % m;
-      if (j >= i) A[i * ld + j] -= A[k * ld + i] * A[k * ld + j];
+    // trailing update of the upper triangle: A[i][j] -= sum_k R[k][i] R[k][j]
+    const int m = N - c1;
+    if (m > 0) {
+      const int mt = (m + 3) / 4;
+      const int npairs = mt * (mt + 1) / 2;
+      for (int t = tid; t < npairs; t += CNT) {
+        // unrank t -> (ti <= tj)
+        int ti = 0, rem = t;
+        while (rem >= mt - ti) {
+          rem -= mt - ti;
+          ++ti;
+        }
+        const int tj = ti + rem;
+        const int i0 = c1 + 4 * ti, j0 = c1 + 4 * tj;
+        double acc[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
+        for (int k = c0; k < c1; ++k) {
+          double a[4], b[4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) a[r] = (i0 + r < N) ? A[k * ld + i0 + r] : 0.0;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) b[c] = (j0 + c < N) ? A[k * ld + j0 + c] : 0.0;
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int i = i0 + r, j = j0 + c;
+            if (i < N && j < N && j >= i) A[i * ld + j] -= acc[r][c];
+          }
+      }
     }
     __syncthreads();
   }
@@ -86,31 +159,56 @@ __global__ void __launch_bounds__(CNT) k_cholinv(const State* st_ro, State* st, 
     return;
   }
 
-  // in-place inverse of the upper triangular R, bottom row first:
-  // X[i][j] = -(sum_{k=i+1..j} R[i][k] X[k][j]) / R[i][i],  X[i][i] = 1 / R[i][i]
-  for (int i = N - 1; i >= 0; --i) {
-    const double rii = A[i * ld + i];
-    double v[(128 + CNT - 1) / CNT + 1];
-    int cnt = 0;
-    for (int j = i + tid; j < N; j += CNT) {
-      double s;
-      if (j == i) {
-        s = 1.0 / rii;
-      } else {
-        s = 0.0;
-        for (int k = i + 1; k <= j; ++k) s += A[i * ld + k] * A[k * ld + j];
-        s = -s / rii;
+  // ------------------------------------------------------------ inverse
+  // X[i][j] (i <= j) is stored at A[j][i] for i < j and in rdiag for i == j.
+  auto X = [&](int i, int j) -> double { return i == j ? rdiag[i] : A[j * ld + i]; };
+  // diagonal blocks: warp p, lane = column, back substitution upward
+  if (warp < np) {
+    const int c0 = warp * NB, c1 = min(N, c0 + NB);
+    const int j = c0 + lane;
+    if (j < c1) {
+      for (int i = j - 1; i >= c0; --i) {
+        double s = 0.0;
+        for (int k = i + 1; k <= j; ++k) s = fma(A[i * ld + k], X(k, j), s);
+        A[j * ld + i] = -s * rdiag[i];
       }
-      v[cnt++] = s;
+    }
+  }
+  __syncthreads();
+  // off-diagonal blocks, level d = q - p
+  for (int d = 1; d < np; ++d) {
+    const int nblk = np - d;  // blocks (p, p + d), p = 0 .. nblk-1
+    // T_p = sum_{r=p+1..p+d} R_pr X_r,p+d
+    for (int idx = tid; idx < nblk * NB * NB; idx += CNT) {
+      const int b = idx / (NB * NB), e = idx % (NB * NB);
+      const int r0 = e / NB, cc = e % NB;
+      const int p = b, q = b + d;
+      const int i = p * NB + r0, j = q * NB + cc;
+      double s = 0.0;
+      if (i < N && j < N) {
+        for (int k = (p + 1) * NB; k <= j; ++k) s = fma(A[i * ld + k], X(k, j), s);
+      }
+      T[b][r0][cc] = s;
     }
     __syncthreads();
-    cnt = 0;
-    for (int j = i + tid; j < N; j += CNT) A[i * ld + j] = v[cnt++];
+    // X_pq = -X_pp T_p (X_pp upper triangular)
+    for (int idx = tid; idx < nblk * NB * NB; idx += CNT) {
+      const int b = idx / (NB * NB), e = idx % (NB * NB);
+      const int r0 = e / NB, cc = e % NB;
+      const int p = b, q = b + d;
+      const int i = p * NB + r0, j = q * NB + cc;
+      if (i < N && j < N) {
+        double s = 0.0;
+        const int kend = min(N, (p + 1) * NB);
+        for (int k = i; k < kend; ++k) s = fma(X(i, k), T[b][k - p * NB][cc], s);
+        A[j * ld + i] = -s;
+      }
+    }
     __syncthreads();
   }
   for (int idx = tid; idx < N * N; idx += CNT) {
     const int i = idx / N, j = idx % N;
-    Rinv[idx] = (j >= i) ? A[i * ld + j] : 0.0;
+    Rinv[idx] = (j > i) ? A[j * ld + i] : (j == i ? rdiag[i] : 0.0);
   }
   if (tid == 0) {
     if (info) *info = 0;
