@@ -108,9 +108,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def algorithmic_bytes(name, N, ng, s):
+def algorithmic_bytes(name, N, ng, s, n):
     """Algorithmic DRAM bytes of one launch (halo re-reads count as zero)."""
     B = N * ng * s
+    hb = 16 * (ng // n) * (n // 2 + 1)  # half-spectrum work array of the FFT passes
     table = {
         "apply_h": 3 * B + 2 * ng * s,            # W, W' in, HW out, V, V - V'
         "rotate_density": 3 * B + 8 * ng,         # trial: W, HW in, W_new out, rho out
@@ -119,11 +120,13 @@ def algorithmic_bytes(name, N, ng, s):
         "gram": 2 * B,                            # trial: W, HW in (split partials are small)
         "gram_reorth": B,                         # second pass: W in
         "gram_sigma": 2 * B,                      # W, HW in
-        "fft_x_fwd": 8 * ng + 16 * ng,
-        "fft_y_fwd": 32 * ng,
-        "fft_z_poisson": 32 * ng,
-        "fft_y_inv": 32 * ng,
-        "fft_x_inv_potential": 16 * ng + 8 * ng * 2 + 8 * ng + s * ng,
+        # half spectrum (nx/2 + 1 complex FP64 columns) read + written per pass
+        "fft_x_fwd": 8 * ng + hb,
+        "fft_y_fwd": 2 * hb,
+        "fft_z_poisson": 2 * hb,
+        "fft_y_inv": 2 * hb,
+        # + rho, Vext, V of the current pair in; V (FP64), V (working type), V - V' out
+        "fft_x_inv_potential": hb + 8 * ng * 3 + 8 * ng + 2 * s * ng,
     }
     return table.get(name)
 
@@ -270,14 +273,14 @@ def run_ours(args):
     peaks, src = measured_peaks()
     # every kernel of the pass is bound by HBM traffic at these sizes (the
     # Gram and rotation contractions use the tensor cores at 10-20 %)
-    b = algorithmic_bytes(name, w.N, ng, esz)
+    b = algorithmic_bytes(name, w.N, ng, esz, w.n)
     ach = b / per_launch_s / 1e9 if b else None
     roof = {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": (ach / peaks["hbm_gbs"]) if ach else None, "traffic": traffic_for(name),
             "peak_source": f"hbm_gbs of {src}"}
     kernels = {}
     for k, (n_, t_) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
-        b = algorithmic_bytes(k, w.N, ng, esz)
+        b = algorithmic_bytes(k, w.N, ng, esz, w.n)
         kernels[k] = {"launches": n_, "ms_total": round(t_, 3), "share": round(t_ / sum(v[1] for v in prof.values()), 4),
                       "gbs": round(b / (t_ / n_ / 1e3) / 1e9, 1) if b else None}
         if k.startswith("gram") and prec == pou.FP32:

@@ -10,6 +10,12 @@
 //   x-forward (reads real rho) -> y-forward -> [z-forward, Poisson scaling,
 //   z-inverse in one pass] -> y-inverse -> x-inverse fused with the potential
 //   and energy epilogue.
+// rho and V_H are real, so only the nx/2 + 1 non-negative x frequencies are
+// kept (the others are their complex conjugates): the x passes transform two
+// real lines a, b as one complex line z = a + i b and separate the spectra,
+//   A(k) = (Z(k) + conj Z(n-k)) / 2,  B(k) = (Z(k) - conj Z(n-k)) / (2 i),
+// (and the inverse merges them back, Z = A + i B with Z(n-k) = conj A(k) +
+// i conj B(k)), and the y and z passes run on nx/2 + 1 columns only.
 #include "pou_internal.cuh"
 
 #include <cmath>
@@ -117,6 +123,7 @@ __device__ double2* fft_lines(double2* src, double2* dst, int nl, int ls, const 
 struct FftArgs {
   AxisDesc ax;
   int nx, ny, nz;
+  int nxh;               // stored x frequencies: nx / 2 + 1
   int lb;
   double2* work;
   const double* rho_in;  // mode 0 source
@@ -153,51 +160,63 @@ __global__ void __launch_bounds__(FNT) k_fft(FftArgs a) {
   const int lb = a.lb;
   double2* b0 = sm;
   double2* b1 = sm + lb * ls;
-  const int nx = a.nx, ny = a.ny, nz = a.nz;
-  const i64 pl = (i64)nx * ny;
+  const int nx = a.nx, ny = a.ny, nz = a.nz, nxh = a.nxh;
+  const i64 plh = (i64)nxh * ny;  // one z plane of the half spectrum
   const bool xaxis = (MODE == 0 || MODE == 4);
-  // line geometry
-  i64 base;   // offset of element 0 of line 0
-  i64 estr;   // element stride
-  int nl;     // lines in this block
+  // line geometry: x passes take nl real lines (rows r0 .. r0 + nl) as
+  // np = ceil(nl / 2) complex lines; y and z passes take nl columns of the
+  // half spectrum
+  i64 base = 0;  // offset of element 0 of line 0 (y, z passes)
+  i64 estr = 0;  // element stride (y, z passes)
+  int nl;        // lines in this block
   int r0 = 0, x0 = 0, yz = 0;
   if (xaxis) {
     r0 = blockIdx.x * lb;
     nl = min(lb, nz * ny - r0);
-    base = (i64)r0 * nx;
-    estr = 1;
   } else {
-    const int nxb = (nx + lb - 1) / lb;
+    const int nxb = (nxh + lb - 1) / lb;
     x0 = (blockIdx.x % nxb) * lb;
     yz = blockIdx.x / nxb;  // z for the y-axis pass, y for the z-axis pass
-    nl = min(lb, nx - x0);
-    base = (MODE == 2) ? (i64)yz * nx + x0 : (i64)yz * pl + x0;
-    estr = (MODE == 2) ? pl : nx;
+    nl = min(lb, nxh - x0);
+    base = (MODE == 2) ? (i64)yz * nxh + x0 : (i64)yz * plh + x0;
+    estr = (MODE == 2) ? plh : nxh;
   }
+  const int ncl = xaxis ? (nl + 1) / 2 : nl;  // complex lines transformed
   const double* rho_src = a.rho_in;
   if (MODE == 0 && a.st) rho_src = a.rho_sel[1 - a.st->cur];
 
   // load
-  for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
-    int line, e;
-    if (xaxis) {
-      line = idx / n;
-      e = idx % n;
-    } else {
-      line = idx % nl;
-      e = idx / nl;
+  if (MODE == 0) {
+    for (int idx = threadIdx.x; idx < ncl * n; idx += blockDim.x) {
+      const int c = idx / n, e = idx % n;
+      const int la = 2 * c, lbb = 2 * c + 1;
+      const double va = rho_src[(i64)(r0 + la) * nx + e];
+      const double vb = lbb < nl ? rho_src[(i64)(r0 + lbb) * nx + e] : 0.0;
+      b0[c * ls + e] = make_double2(va, vb);
     }
-    const i64 g = xaxis ? base + (i64)line * nx + e : base + (i64)e * estr + line;
-    double2 v;
-    if (MODE == 0)
-      v = make_double2(rho_src[g], 0.0);
-    else
-      v = a.work[g];
-    b0[line * ls + e] = v;
+  } else if (MODE == 4) {
+    for (int idx = threadIdx.x; idx < ncl * n; idx += blockDim.x) {
+      const int c = idx / n, k = idx % n;
+      const int la = 2 * c, lbb = 2 * c + 1;
+      const bool lo = k < nxh;
+      const int kk = lo ? k : n - k;
+      double2 fa = a.work[(i64)(r0 + la) * nxh + kk];
+      double2 fb = lbb < nl ? a.work[(i64)(r0 + lbb) * nxh + kk] : make_double2(0.0, 0.0);
+      if (!lo) {
+        fa.y = -fa.y;
+        fb.y = -fb.y;
+      }
+      b0[c * ls + k] = make_double2(fa.x - fb.y, fa.y + fb.x);  // A + i B
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
+      const int line = idx % nl, e = idx / nl;
+      b0[line * ls + e] = a.work[base + (i64)e * estr + line];
+    }
   }
   __syncthreads();
   const bool inv = (MODE >= 3);
-  double2* res = fft_lines(b0, b1, nl, ls, a.ax, inv);
+  double2* res = fft_lines(b0, b1, ncl, ls, a.ax, inv);
   if (MODE == 2) {
     // Poisson kernel 4 pi / |G|^2 (and 1 / Ng of the inverse), G = 0 -> 0
     const int y = yz;
@@ -212,18 +231,23 @@ __global__ void __launch_bounds__(FNT) k_fft(FftArgs a) {
     double2* other = (res == b0) ? b1 : b0;
     res = fft_lines(res, other, nl, ls, a.ax, true);
   }
+  if (MODE == 0) {
+    // separate the spectra of the two real lines, keep k = 0 .. nxh - 1
+    for (int idx = threadIdx.x; idx < ncl * nxh; idx += blockDim.x) {
+      const int c = idx / nxh, k = idx % nxh;
+      const int la = 2 * c, lbb = 2 * c + 1;
+      const double2 zk = res[c * ls + k];
+      const double2 zn = res[c * ls + (k == 0 ? 0 : n - k)];
+      // A = (Z(k) + conj Z(n-k)) / 2,  B = -i (Z(k) - conj Z(n-k)) / 2
+      a.work[(i64)(r0 + la) * nxh + k] = make_double2(0.5 * (zk.x + zn.x), 0.5 * (zk.y - zn.y));
+      if (lbb < nl) a.work[(i64)(r0 + lbb) * nxh + k] = make_double2(0.5 * (zk.y + zn.y), -0.5 * (zk.x - zn.x));
+    }
+    return;
+  }
   if (MODE != 4) {
     for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
-      int line, e;
-      if (xaxis) {
-        line = idx / n;
-        e = idx % n;
-      } else {
-        line = idx % nl;
-        e = idx / nl;
-      }
-      const i64 g = xaxis ? base + (i64)line * nx + e : base + (i64)e * estr + line;
-      a.work[g] = res[line * ls + e];
+      const int line = idx % nl, e = idx / nl;
+      a.work[base + (i64)e * estr + line] = res[line * ls + e];
     }
     return;
   }
@@ -240,8 +264,9 @@ __global__ void __launch_bounds__(FNT) k_fft(FftArgs a) {
   double s_ext = 0.0, s_h = 0.0, s_x = 0.0;
   for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
     const int line = idx / n, e = idx % n;
-    const i64 g = base + (i64)line * nx + e;
-    const double vh = res[line * ls + e].x;
+    const i64 g = (i64)(r0 + line) * nx + e;
+    const double2 zv = res[(line >> 1) * ls + e];
+    const double vh = (line & 1) ? zv.y : zv.x;
     if (a.vh_out) {
       a.vh_out[g] = vh;
       continue;
@@ -441,6 +466,7 @@ int launch_potential(const FftPlan& p, const PotArgs<T>& pa, cudaStream_t s) {
   a.nx = nx;
   a.ny = ny;
   a.nz = nz;
+  a.nxh = nx / 2 + 1;
   a.work = pa.work;
   a.rho_in = pa.rho_x;
   a.g2x = p.g2[0];
@@ -479,8 +505,9 @@ int launch_potential(const FftPlan& p, const PotArgs<T>& pa, cudaStream_t s) {
   }
   const int lbx = p.lb[0], lby = p.lb[1], lbz = p.lb[2];
   const int gx = (nz * ny + lbx - 1) / lbx;
-  const int gy = ((nx + lby - 1) / lby) * nz;
-  const int gz = ((nx + lbz - 1) / lbz) * ny;
+  const int nxh = nx / 2 + 1;
+  const int gy = ((nxh + lby - 1) / lby) * nz;
+  const int gz = ((nxh + lbz - 1) / lbz) * ny;
   launch_axis<0>(p, 0, a, gx, s);
   launch_axis<1>(p, 1, a, gy, s);
   launch_axis<2>(p, 2, a, gz, s);
