@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--prep-steps", type=int, default=200,
+                    help="untimed steps from the random start before the warm-up, so that the timed steps "
+                         "are in the steady regime of a run")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="l30_g160_n128")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
@@ -56,6 +59,18 @@ def parse():
 
 
 # --------------------------------------------------------------- helpers
+def job_rate(ms, K, world, device="cuda"):
+    """Whole-job rate of K steps per rank: the slowest rank's time (max over
+    ranks, a collective on the timing only) and world * K steps over it."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * K / (ms / 1e3)
+
+
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -228,6 +243,8 @@ def run_ours(args):
     s.set_orbitals(U0)
     K, W = args.steps, args.warmup
     fe = args.force_every
+    if args.prep_steps > 0:
+        s.iterate(args.prep_steps)
 
     def step(i):
         s.iterate(1)
@@ -244,10 +261,12 @@ def run_ours(args):
     torch.cuda.synchronize()
     launches0 = s.launch_count()
     passes = 0
+    second = 0
     ev0.record(stream)
     for i in range(K):
         rep = s.iterate(1)
         passes += rep["passes"]
+        second += rep["second_passes"]
         if fe > 0 and (i + 1) % fe == 0:
             s.backward(None, 1.0, None, atoms=True)
     ev1.record(stream)
@@ -258,11 +277,7 @@ def run_ours(args):
     prof = s.profile()
     s.set_profiling(False)
     E_final = s.energy()["total"]
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * K / (ms / 1e3)
+    ms, value = job_rate(ms, K, world)
 
     # roofline of the dominant kernel (live CUDA-event times on the library's stream)
     esz = 4 if prec == pou.FP32 else 8
@@ -279,16 +294,22 @@ def run_ours(args):
             "frac": (ach / peaks["hbm_gbs"]) if ach else None, "traffic": traffic_for(name),
             "peak_source": f"hbm_gbs of {src}"}
     kernels = {}
+    # kernels of the second Cholesky-QR pass are launched every pass and return
+    # at once unless the pass is taken: rates use the passes actually taken
+    gated = {"gram_reorth", "rotate_reorth"}
     for k, (n_, t_) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
         b = algorithmic_bytes(k, w.N, ng, esz, w.n)
+        eff = second if k in gated else n_
         kernels[k] = {"launches": n_, "ms_total": round(t_, 3), "share": round(t_ / sum(v[1] for v in prof.values()), 4),
-                      "gbs": round(b / (t_ / n_ / 1e3) / 1e9, 1) if b else None}
-        if k.startswith("gram") and prec == pou.FP32:
+                      "gbs": round(b / (t_ / eff / 1e3) / 1e9, 1) if (b and eff) else None}
+        if k in gated:
+            kernels[k]["taken"] = eff
+        if k in ("gram", "gram_reorth", "gram_plain") and prec == pou.FP32 and eff:
             # tensor-core rate of the TF32 split products actually issued (two
             # M=N=128, K=8 MMAs per 8 grid points: 4 * 128^2 * ng flops) and the
             # Gram's own algorithmic flops (upper triangle)
-            kernels[k]["tensor_tflops_issued"] = round(4 * 128 * 128 * ng / (t_ / n_ / 1e3) / 1e12, 1)
-            kernels[k]["gram_tflops"] = round(gram_flops(w.N, ng) / (t_ / n_ / 1e3) / 1e12, 2)
+            kernels[k]["tensor_tflops_issued"] = round(4 * 128 * 128 * ng / (t_ / eff / 1e3) / 1e12, 1)
+            kernels[k]["gram_tflops"] = round(gram_flops(w.N, ng) / (t_ / eff / 1e3) / 1e12, 2)
     iter_kernels = [k for k in prof if k not in ("density", "forces", "potential_local", "convert", "scale_copy")]
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -298,8 +319,10 @@ def run_ours(args):
                    "atoms": w.n_atoms, "N": w.N, "precision": "mixed: FP32 bulk, FP64 Cholesky/FFT/energies"
                    if prec == pou.FP32 else "FP64", "bb_variant": args.bb_variant, "forces_every": fe,
                    "l2": "inputs larger than L2 (orbital block %.2f GB)" % (w.N * ng * esz / 1e9),
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
-        "passes": passes, "gpu_launches": launches, "roofline": roof, "kernels": kernels,
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "state": f"after {args.prep_steps} untimed steps from the random start"},
+        "passes": passes, "second_cholesky_qr_passes": second, "gpu_launches": launches, "roofline": roof,
+        "kernels": kernels,
         "energy_final": E_final, "clocks": clocks, "input_generation_s": round(gen_s, 1),
     }
     out["_iter_kernels"] = iter_kernels
@@ -326,7 +349,7 @@ def run_ours(args):
     if not args.no_e2e:
         Kh = max(5, min(K, 20))
         host = torch.empty(U0.shape, dtype=torch.float32 if prec == pou.FP32 else torch.float64, pin_memory=True)
-        host.copy_(torch.from_numpy(U0))
+        s.get_orbitals(host)  # the orbitals the timed steps ended with: same regime
         outh = torch.empty_like(host, pin_memory=True)
         torch.cuda.synchronize()
         t = time.perf_counter()
@@ -337,7 +360,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         te = time.perf_counter() - t
         blk = host.numel() * host.element_size()
-        out["e2e"] = {"value": world * Kh / te, "unit": UNIT, "steps": Kh,
+        out["e2e"] = {"value": job_rate(te * 1e3, Kh, world)[1], "unit": UNIT, "steps": Kh,
                       "h2d_bytes_per_step": blk / Kh, "d2h_bytes_per_step": blk / Kh + 512,
                       "includes": "set_orbitals (pinned host block, Cholesky-QR, potential, energy) + "
                                   "steps + get_orbitals to pinned host"}
@@ -359,41 +382,79 @@ def run_ours(args):
 
 
 def time_to_tolerance(pou, torch, w, R, Z, U0, stream, args):
-    """Wall time until |E_l - E*| <= 1e-6 Ha for the FP64 and mixed forms."""
+    """Wall time until |E_l - E*| <= 1e-6 Ha: the FP64 form, the mixed form,
+    and the mixed form refined in FP64 once its progress stalls.
+
+    E* is the lowest FP64-form energy within ttt_max steps.  FP32 storage of the
+    orbitals perturbs the energy by ~1e-8 Ha per step on these systems, while
+    near E* the iteration gains ~1e-9 Ha per step, so the mixed form alone
+    stalls some 1e-6 Ha above E*; the refined path switches to the FP64 form
+    (same orbitals, re-orthonormalised in FP64) when the mixed form's energy
+    falls by less than switch_rel |E| over 100 steps.
+    """
     res = {}
     curves = {}
-    for prec, label in ((pou.FP64, "fp64"), (pou.FP32, "mixed")):
+    chunk = 50
+
+    def run(prec, U, max_steps, stop=None):
         s = make_solver(pou, w, prec, stream.cuda_stream, args.bb_variant)
         s.set_atoms(R, Z, w.width)
-        s.set_orbitals(U0)
+        s.set_orbitals(U)
         torch.cuda.synchronize()
         t = time.perf_counter()
-        times, done = [], 0
-        while done < args.ttt_max:
-            s.iterate(50)
-            done += 50
+        times, done, last = [], 0, None
+        while done < max_steps:
+            rep = s.iterate(chunk)
+            done += chunk
             times.append((done, time.perf_counter() - t))
+            if stop is not None and done % 100 == 0:
+                if last is not None and stop(last, rep["energy"]):
+                    break
+                last = rep["energy"]
         E, _ = s.history()
+        return s, E, times
+
+    for prec, label in ((pou.FP64, "fp64"), (pou.FP32, "mixed")):
+        s, E, times = run(prec, U0, args.ttt_max)
         curves[label] = (E, times)
         s.close()
     E64 = curves["fp64"][0]
     Estar = float(np.min(E64))
-    for label, (E, times) in curves.items():
+
+    def first_hit(E, times, offset_s=0.0, offset_it=0):
         hit = np.nonzero(np.abs(E - Estar) <= 1e-6)[0]
         if len(hit) == 0:
-            res[label] = {"reached": False, "iterations": len(E), "final_error": float(E[-1] - Estar)}
-            continue
+            return {"reached": False, "iterations": offset_it + len(E), "final_error": float(E[-1] - Estar)}
         it = int(hit[0]) + 1
-        # wall time at that iteration, interpolated within the 50-step chunk
-        for d, tt in times:
+        for d, tt in times:  # wall time at that iteration, interpolated within the chunk
             if d >= it:
                 prev = [x for x in times if x[0] < d]
                 t0, d0 = (prev[-1][1], prev[-1][0]) if prev else (0.0, 0)
                 sec = t0 + (tt - t0) * (it - d0) / (d - d0)
                 break
-        res[label] = {"reached": True, "iterations": it, "seconds": sec}
+        return {"reached": True, "iterations": offset_it + it, "seconds": offset_s + sec}
+
+    for label, (E, times) in curves.items():
+        res[label] = first_hit(E, times)
+    # mixed, then FP64 from the mixed iterate once it stalls
+    switch_rel = 3e-8
+    s32, E32, t32 = run(pou.FP32, U0, args.ttt_max,
+                        stop=lambda prev, cur: (prev - cur) < switch_rel * abs(cur))
+    U = s32.get_orbitals()
+    s32.close()
+    s64, E64b, t64b = run(pou.FP64, U, args.ttt_max)
+    s64.close()
+    hit32 = first_hit(E32, t32)
+    if hit32["reached"]:
+        res["mixed_then_fp64"] = dict(hit32, switched_at=None)
+    else:
+        r = first_hit(E64b, t64b, offset_s=t32[-1][1], offset_it=len(E32))
+        r["switched_at"] = {"mixed_steps": len(E32), "seconds": t32[-1][1], "error": float(E32[-1] - Estar)}
+        res["mixed_then_fp64"] = r
     res["E_star"] = Estar
     res["E_star_definition"] = f"lowest FP64-form energy within {args.ttt_max} steps"
+    res["switch_rule"] = f"mixed energy falls by less than {switch_rel:g} |E| over 100 steps"
+    res["workload"] = args.workload
     return res
 
 
