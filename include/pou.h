@@ -171,7 +171,11 @@ pou_status pou_get_density(pou_ctx* ctx, double* rho, int on_device);
 pou_status pou_get_potential(pou_ctx* ctx, double* V, int on_device);
 
 /* ||grad E||_F = sqrt(tr<G^T G>), G = HW - W Sigma, Sigma = <(HW)^T W>
- * (Eq. gra), of the current orbitals. */
+ * (Eq. gra, Sec. 2.2), of the current orbitals W and their HW, into *out
+ * (host).  Sigma is formed on the device in the working precision; G is
+ * formed point by point and its squares summed in FP64.  Synchronises the
+ * context's stream.  POU_EINVAL when no orbitals are set.  Overwrites the
+ * context's N x N scratch matrix (not part of the iteration state). */
 pou_status pou_gradient_norm(pou_ctx* ctx, double* out);
 
 /* Energy of an arbitrary block U (not orthonormalised, Eq. energy) without

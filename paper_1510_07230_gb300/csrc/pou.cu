@@ -1150,9 +1150,54 @@ pou_status pou_get_potential(pou_ctx* c, double* V, int on_device) {
   return POU_OK;
 }
 
+extern "C++" {
+namespace {
+// Sigma = <W^T HW> of the current pair (general Gram into c->S), then the
+// residual partials into c->epart.
+template <typename T>
+pou_status gradient_norm_impl(pou_ctx* c, int cur, double* out) {
+  cudaStream_t s = c->stream;
+  GramArgs<T> g{};
+  g.A = tp<T>(c->W[cur]);
+  g.B = tp<T>(c->HW[cur]);
+  g.ng = c->ng;
+  g.N = c->N;
+  g.split = c->split;
+  launch_gram<T>(g, s);
+  int nsplit, npair;
+  i64 chunk;
+  gram_layout<T>(c->ng, c->N, true, &nsplit, &npair, &chunk);
+  GramReduceArgs r{};
+  r.split = c->split;
+  r.nsplit = nsplit;
+  r.npair = npair;
+  r.ST = gram_supertile<T>();
+  r.N = c->N;
+  r.general = 1;
+  r.dV = c->dV;
+  r.S = c->S;
+  launch_gram_reduce(r, s);  // S_ij = <w_i, hw_j> = Sigma_ji
+  const int nb = launch_residual<T>(tp<T>(c->W[cur]), tp<T>(c->HW[cur]), c->S, c->N, c->ng, c->epart,
+                                    c->neblk_max * NE, s);
+  std::vector<double> h(nb);
+  CK(cudaMemcpyAsync(h.data(), c->epart, nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  double t = 0.0;
+  for (double v : h) t += v;
+  *out = std::sqrt(c->dV * t);
+  return POU_OK;
+}
+}  // namespace
+}  // extern "C++"
+
 pou_status pou_gradient_norm(pou_ctx* c, double* out) {
-  if (!c || !out) return POU_EINVAL;
-  return fail(c, POU_EINVAL, "gradient norm not available in this build");
+  ProfScope prof_scope(c);
+  if (!c || !out) return fail(c, POU_EINVAL, "bad argument");
+  if (!c->have_orbitals) return fail(c, POU_EINVAL, "no orbitals set");
+  int cur;
+  pou_status e = cur_index(c, &cur);
+  if (e != POU_OK) return e;
+  return c->dt == 1 ? gradient_norm_impl<float>(c, cur, out) : gradient_norm_impl<double>(c, cur, out);
 }
 
 pou_status pou_evaluate(pou_ctx* c, const void* U, int dtype, int on_device, pou_energy_terms* out) {

@@ -166,6 +166,10 @@ void launch_rotate(const RotArgs<T>& a, cudaStream_t s);
 
 template <typename T>
 void launch_density(const T* U, i64 ng, int N, double* rho, cudaStream_t s);
+// ||HW - W Sigma||_F^2 / dV partials (Eq. gra), one per CTA; returns the CTA count.
+template <typename T>
+int launch_residual(const T* W, const T* HW, const double* Sig, int N, i64 ng, double* part, int max_blocks,
+                    cudaStream_t s);
 void launch_convert_f64_f32(const double* in, float* out, i64 n, cudaStream_t s);
 void launch_convert_f32_f64(const float* in, double* out, i64 n, cudaStream_t s);
 template <typename T>

@@ -370,6 +370,63 @@ def test_energy_criterion_stops(P):
     s.close()
 
 
+# ------------------------------------------------------------------ a10: Kohn-Sham residual
+def _oracle_gradient(W, R, Z, w):
+    cfg = ocfg(w.n, w.L, w.N, order=w.order)
+    vext = O.vext_gaussians(cfg, R, Z, w.width)
+    HW = O.apply_h(W, O.total_potential(O.density(W), vext, cfg), cfg)
+    return O.gradient_residual(W, HW, cfg)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("steps", [0, 40, 400])
+def test_gradient_norm_matches_oracle(P, precision, steps):
+    """|HW - W Sigma|_F (Eq. gra) of the current orbitals, from random start to
+    near convergence.  The oracle runs on the returned orbitals; in the FP32
+    form HW is rounded to FP32 (2^-24 |HW| per point), which bounds the
+    absolute error by about 1e-6 |HW|_F."""
+    w, R, Z, U0, s = _workload_solver(P, "l10_g32_n4", precision=precision)
+    s.set_orbitals(U0)
+    if steps:
+        s.iterate(steps)
+    W = s.get_orbitals()
+    got, ref = s.gradient_norm(), _oracle_gradient(W, R, Z, w)
+    tol = 1e-9 * max(1.0, ref) if precision == 0 else 3e-3 * ref + 2e-5
+    assert abs(got - ref) <= tol, (got, ref)
+    s.close()
+
+
+def test_gradient_norm_odd_sizes_and_128_orbitals(P):
+    """Ragged point chunks (ng not a multiple of 64) and the largest block."""
+    for n, N in [((7, 5, 3), 3), ((12, 10, 9), 128)]:
+        L = (5.0, 4.0, 3.5)
+        cfg = ocfg(n, L, N)
+        R = np.array([[1.0, 1.5, 2.0]])
+        Z = np.array([2.0])
+        s = solver(P, n, L, N)
+        s.set_atoms(R, Z, 0.8)
+        s.set_orbitals(inputs.random_orbitals(7, N, cfg.n))
+        W = s.get_orbitals()
+        vext = O.vext_gaussians(cfg, R, Z, 0.8)
+        HW = O.apply_h(W, O.total_potential(O.density(W), vext, cfg), cfg)
+        ref = O.gradient_residual(W, HW, cfg)
+        assert abs(s.gradient_norm() - ref) <= 1e-10 * ref
+        s.close()
+
+
+def test_iterate_gradient_criterion_stops(P):
+    """grad_tol: iterate stops once |grad E| < tol (checked every 10 steps)."""
+    w, R, Z, U0, s = _workload_solver(P, "l10_g32_n4")
+    s.set_orbitals(U0)
+    rep = s.iterate(5000, grad_tol=1e-4)
+    assert rep["converged"] == 2 and rep["status"] == P.OK  # 2: the gradient criterion
+    assert rep["grad_norm"] < 1e-4
+    g = s.gradient_norm()
+    assert g < 1e-4
+    assert abs(g - _oracle_gradient(s.get_orbitals(), R, Z, w)) < 1e-9
+    s.close()
+
+
 # ------------------------------------------------------------------ Algorithm M: subspace diagonalisation
 def test_subspace_diagonalisation_fp64_matches_oracle(P):
     """n_diag = 20 (Sec. 3.3): three rotations W <- W P within the first 70 steps."""

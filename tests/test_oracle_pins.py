@@ -178,6 +178,40 @@ def test_energy_plane_wave_and_rotation_invariance():
     assert abs(cfg2.dV * O.density(W).sum() - 2 * 3) < 1e-11
 
 
+@pytest.mark.parametrize("order", [2, 4])
+def test_gradient_residual_two_plane_waves(order):
+    """Eq. gra on w = a phi_1 + b phi_2 (free particle, eigenvalues e_1, e_2 of
+    H = -1/2 Lap_h): Sigma = a^2 e_1 + b^2 e_2 and |G| = |a b| |e_1 - e_2|;
+    any rotation of (phi_1, phi_2) spans an invariant subspace, so G = 0."""
+    cfg = O.Config(n=(12, 10, 9), L=(6.0, 5.5, 4.0), order=order, N=1, hartree=0, exchange=0)
+    m1, m2 = (1, 0, 0), (0, 2, 1)
+    e = [0.5 * sum(_symbol(order, m[a], cfg.n[a], cfg.h[a]) for a in range(3)) for m in (m1, m2)]
+    phis = []
+    for m in (m1, m2):
+        u = _plane(cfg, m)
+        phis.append(u / math.sqrt(cfg.dV * np.sum(u * u)))
+    V0 = np.zeros(cfg.shape)
+    a, b = 0.6, -0.8
+    w = (a * phis[0] + b * phis[1])[None]
+    g = O.gradient_residual(w, O.apply_h(w, V0, cfg), cfg)
+    assert abs(g - abs(a * b) * abs(e[0] - e[1])) < 1e-12 * max(e)
+    W = np.stack([a * phis[0] + b * phis[1], -b * phis[0] + a * phis[1]])
+    assert O.gradient_residual(W, O.apply_h(W, V0, cfg), cfg) < 1e-12 * max(e)
+
+
+def test_gradient_residual_is_the_projected_norm():
+    """For orthonormal W and symmetric H, G = (I - W W^T) H W, so
+    |G|^2 = |HW|^2 - |Sigma|^2 (Pythagoras on the projector)."""
+    cfg = O.Config(n=(10, 9, 8), L=(5.0, 4.5, 4.0), order=4, N=4)
+    W, _, _ = O.cholesky_qr(inputs.random_orbitals(21, 4, cfg.n), cfg)
+    V = np.random.default_rng(3).standard_normal(cfg.shape)
+    HW = O.apply_h(W, V, cfg)
+    hw2 = cfg.dV * float(np.sum(HW * HW))
+    sig = cfg.dV * (W.reshape(4, -1) @ HW.reshape(4, -1).T)
+    exact = math.sqrt(hw2 - float(np.sum(sig * sig)))
+    assert abs(O.gradient_residual(W, HW, cfg) - exact) < 1e-10 * exact
+
+
 def _free_levels(cfg, N):
     lv = sorted(0.5 * sum(_symbol(cfg.order, m[a], cfg.n[a], cfg.h[a]) for a in range(3))
                 for m in itertools.product(*(range(v) for v in cfg.n)))
