@@ -398,7 +398,7 @@ def test_gradient_norm_matches_oracle(P, precision, steps):
 
 def test_gradient_norm_odd_sizes_and_128_orbitals(P):
     """Ragged point chunks (ng not a multiple of 64) and the largest block."""
-    for n, N in [((7, 5, 3), 3), ((12, 10, 9), 128)]:
+    for n, N in [((5, 6, 3), 3), ((12, 10, 9), 128)]:
         L = (5.0, 4.0, 3.5)
         cfg = ocfg(n, L, N)
         R = np.array([[1.0, 1.5, 2.0]])
