@@ -150,8 +150,11 @@ def gram_flops(N, ng):
     return N * (N + 1) * ng  # upper triangle, one FMA = 2 flops
 
 
-def traffic_for(kernel):
-    """DRAM bytes per launch from a committed ncu summary, if it is current."""
+def traffic_for(kernel, units):
+    """DRAM bytes per launch from a committed ncu capture, if it is current:
+    the captured bytes per orbital-grid-point unit times this launch's units
+    (N * Ng; the kernels sweep each orbital independently, so traffic grows in
+    proportion)."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
@@ -162,7 +165,7 @@ def traffic_for(kernel):
             return None
         src = os.path.join(ROOT, ent["source"])
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        return ent["bytes_per_launch"] if h == ent["source_sha"] else None
+        return ent["bytes_per_unit"] * units if h == ent["source_sha"] else None
     except Exception:
         return None
 
@@ -291,7 +294,7 @@ def run_ours(args):
     b = algorithmic_bytes(name, w.N, ng, esz, w.n)
     ach = b / per_launch_s / 1e9 if b else None
     roof = {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": (ach / peaks["hbm_gbs"]) if ach else None, "traffic": traffic_for(name),
+            "frac": (ach / peaks["hbm_gbs"]) if ach else None, "traffic": traffic_for(name, w.N * ng),
             "peak_source": f"hbm_gbs of {src}"}
     kernels = {}
     # kernels of the second Cholesky-QR pass are launched every pass and return
