@@ -49,7 +49,9 @@ __global__ void __launch_bounds__(KNT) k_control(CtrlArgs a) {
   for (int idx = tid; idx < N * NP; idx += KNT) {
     const int i = idx / NP, k = idx % NP;
     if (k == P_SIGP) {
-      part[idx] = a.init ? 0.0 : a.sigma[cur][i];  // refresh: the eigenvalue
+      // the sigma' the H-apply used (refresh: the eigenvalue), as it was rounded there
+      const double sp = a.init ? 0.0 : a.sigma[cur][i];
+      part[idx] = a.fp32 ? (double)(float)sp : sp;
       continue;
     }
     const double* src = a.tilepart + (i64)i * a.ntile * NPT + k;

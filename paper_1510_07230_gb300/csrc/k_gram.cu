@@ -777,8 +777,9 @@ int rotate_grid(i64 ng, int elem_bytes) {
 template <typename T>
 void launch_rotate(const RotArgs<T>& a, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
-    if (a.general && !a.trial) {
-      // dense P of Algorithm M: CUDA cores, exact FP32 products
+    if (a.general) {
+      // dense P of Algorithm M: CUDA cores, exact FP32 products (the
+      // tensor-core rotation takes upper triangular R^-1 only)
       const int nchunks = (int)((a.ng + RP - 1) / RP);
       prof_begin(rotate_prof_name(a.trial, a.src_trial_slot, a.src_cur_slot), s);
       k_rotate_f32_cc<<<std::min(nchunks, 2 * 152), RNT, rotate_f32_smem(), s>>>(a, nchunks);

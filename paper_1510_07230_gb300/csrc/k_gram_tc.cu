@@ -3,8 +3,10 @@
 // Wt = (1 + tau sigma_i) w_i - tau hw_i, of the second-pass block, or of a
 // caller's block), for N <= 128 orbitals.
 //
-// Precision: every FP32 value x of the block is split into two TF32 numbers,
-// x = hi + lo + O(2^-22 x), hi = tf32(x), lo = tf32(x - hi).  Per K step two
+// Precision: every FP32 value x of the block is split into hi = tf32(x) and
+// lo = x - hi (exact in FP32); the tensor core reads the leading TF32 bits of
+// lo (truncation), so x = hi + lo + O(2^-22 x), the same split the
+// tensor-core rotation applies to the block it rotates.  Per K step two
 // MMAs of shape M = N = 128, K = 8 accumulate D += Hi Hi^T + Hi (2 Lo)^T, so
 // that the symmetric part (D + D^T) / 2 = Hi Hi^T + Hi Lo^T + Lo Hi^T is the
 // Gram to about 2^-21 relative per product (random sign); the reduction
@@ -54,7 +56,7 @@ constexpr int OFF_BAR = OFF_DIAG + 128 * 8;
 constexpr int NBAR = 2 * STAGES + 5;
 constexpr int OFF_MISC = OFF_BAR + NBAR * 8;
 constexpr int OFF_COEF = OFF_MISC + 16;
-constexpr int SMEM_BYTES = OFF_COEF + 128 * 4 + 1024;  // + alignment slack
+constexpr int SMEM_BYTES = OFF_COEF + 128 * 8 + 1024;  // + alignment slack
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t COL_SUM = 256, COL_ERR = 384;
 constexpr uint32_t IDESC = tc::idesc_tf32(128, 128);
@@ -71,8 +73,11 @@ __device__ __forceinline__ void two_sum_into(float& s, float& c, float v) {
 }
 
 // VEC: rows start on 16-byte boundaries and ng % 4 == 0 (float4 loads); the
-// other instantiation loads element by element.
-template <bool VEC>
+// other instantiation loads element by element.  TRIAL: the block is the
+// trial point formed from W[cur] and HW[cur]; its diagonal is left to the
+// reduction (the FP64 norm from the H-apply sums), which frees the
+// producers' diagonal registers for the double-float split.
+template <bool VEC, bool TRIAL>
 __global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb) {
   extern __shared__ unsigned char smem_raw[];
   if (a.st && a.st->done) return;
@@ -92,7 +97,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb)
   const uint32_t fin_bar = bar0 + 8u * (2 * STAGES + 4);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + OFF_MISC);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + OFF_MISC + 4);
-  float* coefs = reinterpret_cast<float*>(smem + OFF_COEF);
+  float2* coefs = reinterpret_cast<float2*>(smem + OFF_COEF);  // 1 + tau sigma_i as (hi, lo)
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int N = a.N;
@@ -106,14 +111,19 @@ __global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb)
 
   const float* Wa;
   const float* Ha = nullptr;
-  float tauF = 0.f;
-  if (a.trial) {
+  float tauH = 0.f, tauL = 0.f;
+  if (TRIAL) {
     const int cur = a.st->cur;
     Wa = a.W[cur];
     Ha = a.HW[cur];
     const double tau = a.st->tau_trial;
-    tauF = (float)tau;
-    for (int r = tid; r < 128; r += NTHR) coefs[r] = r < N ? (float)(1.0 + tau * a.sigma[cur][r]) : 0.f;
+    tauH = (float)tau;
+    tauL = (float)(tau - (double)tauH);
+    for (int r = tid; r < 128; r += NTHR) {
+      const double cf = r < N ? 1.0 + tau * a.sigma[cur][r] : 0.0;
+      const float ch = (float)cf;
+      coefs[r] = make_float2(ch, (float)(cf - (double)ch));
+    }
   } else if (a.src_trial_slot) {
     Wa = a.W[1 - a.st->cur];
   } else {
@@ -161,7 +171,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb)
           // ng % 4 == 0: a chunk is either wholly inside the row or past its end
           if (p < ng) {
             wv[q] = __ldg(reinterpret_cast<const float4*>(Wa + off));
-            if (Ha) hv[q] = __ldg(reinterpret_cast<const float4*>(Ha + off));
+            if (TRIAL) hv[q] = __ldg(reinterpret_cast<const float4*>(Ha + off));
           }
         } else {
           float t[4] = {0.f, 0.f, 0.f, 0.f}, u[4] = {0.f, 0.f, 0.f, 0.f};
@@ -169,7 +179,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb)
           for (int e = 0; e < 4; ++e)
             if (p + e < ng) {
               t[e] = Wa[off + e];
-              if (Ha) u[e] = Ha[off + e];
+              if (TRIAL) u[e] = Ha[off + e];
             }
           wv[q] = make_float4(t[0], t[1], t[2], t[3]);
           hv[q] = make_float4(u[0], u[1], u[2], u[3]);
@@ -187,21 +197,26 @@ __global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb)
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int r = r0 + 32 * q;
-        float x[4] = {w[q].x, w[q].y, w[q].z, w[q].w};
-        if (Ha) {
-          const float cf = coefs[r];
+        const float x[4] = {w[q].x, w[q].y, w[q].z, w[q].w};
+        float hi[4], lo[4];
+        if (TRIAL) {
+          const float2 cf = coefs[r];
           const float hv4[4] = {h[q].x, h[q].y, h[q].z, h[q].w};
 #pragma unroll
-          for (int e = 0; e < 4; ++e) x[e] = cf * x[e] - tauF * hv4[e];
-        }
-        float hi[4], lo[4], sq = 0.f;
+          for (int e = 0; e < 4; ++e) {
+            tc::trial_split(cf.x, cf.y, x[e], tauH, tauL, hv4[e], hi[e], lo[e]);
+            lo[e] *= 2.0f;
+          }
+        } else {
+          float sq = 0.f;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          hi[e] = tc::to_tf32(x[e]);
-          lo[e] = 2.0f * tc::to_tf32(x[e] - hi[e]);
-          sq = fmaf(x[e], x[e], sq);
+          for (int e = 0; e < 4; ++e) {
+            hi[e] = tc::to_tf32(x[e]);
+            lo[e] = 2.0f * (x[e] - hi[e]);  // exact; the tensor core reads its leading TF32 bits
+            sq = fmaf(x[e], x[e], sq);
+          }
+          two_sum_into(ds[q], dc[q], sq);
         }
-        two_sum_into(ds[q], dc[q], sq);
         const int off = r * 128 + ((c ^ (r & 7)) << 4);
         *reinterpret_cast<float4*>(hi_t + off) = make_float4(hi[0], hi[1], hi[2], hi[3]);
         *reinterpret_cast<float4*>(lo_t + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
@@ -220,7 +235,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb)
     }
     // the eight lanes that share a row hold its diagonal in parts
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < (TRIAL ? 0 : 4); ++q) {
 #pragma unroll
       for (int o = 1; o <= 4; o <<= 1) {
         const float os = __shfl_xor_sync(0xffffffffu, ds[q], o);
@@ -357,8 +372,10 @@ bool gram_tc_eligible(const GramArgs<float>& a) {
 
 void configure_gram_tc() {
   if (g_configured) return;
-  cudaFuncSetAttribute(k_gram_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-  cudaFuncSetAttribute(k_gram_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  cudaFuncSetAttribute(k_gram_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  cudaFuncSetAttribute(k_gram_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  cudaFuncSetAttribute(k_gram_tc<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  cudaFuncSetAttribute(k_gram_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   g_configured = true;
 }
 
@@ -375,10 +392,16 @@ void launch_gram_tc(const GramArgs<float>& a, int nsplit, cudaStream_t s) {
   } else {
     vec = vec && aligned(a.A);
   }
-  if (vec)
-    k_gram_tc<true><<<nsplit, NTHR, SMEM_BYTES, s>>>(a, nkb);
-  else
-    k_gram_tc<false><<<nsplit, NTHR, SMEM_BYTES, s>>>(a, nkb);
+  if (a.trial) {
+    if (vec)
+      k_gram_tc<true, true><<<nsplit, NTHR, SMEM_BYTES, s>>>(a, nkb);
+    else
+      k_gram_tc<false, true><<<nsplit, NTHR, SMEM_BYTES, s>>>(a, nkb);
+  } else if (vec) {
+    k_gram_tc<true, false><<<nsplit, NTHR, SMEM_BYTES, s>>>(a, nkb);
+  } else {
+    k_gram_tc<false, false><<<nsplit, NTHR, SMEM_BYTES, s>>>(a, nkb);
+  }
   prof_end(s);
 }
 

@@ -1,46 +1,54 @@
-// Rotation W_new = Wt R^-1 of the FP32 form (Orth by Cholesky-QR, Sec. 3.2;
-// the subspace rotation W P of Algorithm M, Sec. 3.3) on the 5th-generation
-// tensor cores, fused with the density rho = f sum_j w_new_j^2 (Sec. 2), for
-// N <= 128 orbitals.
+// Rotation W_new = Wt R^-1 of the FP32 form (Orth by Cholesky-QR, Sec. 3.2)
+// on the 5th-generation tensor cores, fused with the density
+// rho = f sum_j w_new_j^2 (Sec. 2), for N <= 128 orbitals and upper
+// triangular R^-1 (the dense subspace rotation of Algorithm M runs on the CUDA
+// cores).
 //
 // Split of the work.  Output j at point p is
-//   w_new_j(p) = sum_{i != j} x_i(p) R_ij  +  R_jj x_j(p),
-// x = Wt (trial: (1 + tau sigma_i) w_i - tau hw_i) or the block itself.  The
+//   w_new_j(p) = sum_{i < j} x_i(p) R_ij  +  R_jj x_j(p),
+// x = Wt (trial: (1 + tau sigma_i) w_i - tau hw_i, rounded once to FP32, the
+// same value the trial Gram matrix is formed from) or the block itself.  The
 // off-diagonal sum runs on the tensor cores as D = X R_off with M = 128 grid
-// points (tensor-memory lanes), N = 128 outputs j (columns) and K = 128
-// orbitals i, both operands split into TF32 pairs: D = Xhi Rhi + Xhi Rlo +
-// Xlo Rhi, which carries the sum to about 2^-21 of its own size.  The tensor
-// core adds into its FP32 accumulator with truncation (a bias toward zero of
-// a fraction of an ulp per accumulation), so the dominant Xhi Rhi part is
-// kept in two accumulators (orbitals 0-63 and 64-127, eight accumulations
-// each), the small cross terms in a third, and the three are added on the
-// CUDA cores with round-to-nearest.  The self term is formed on the CUDA
-// cores from w and hw directly with double-float coefficients and stored
-// with unbiased (dithered) rounding, as the CUDA-core rotation does, because
-// near convergence the corrections that keep each orbital normalised are
-// below half an ulp of its elements.
+// points (tensor-memory lanes), N = outputs j (columns) and K = orbitals i,
+// both operands split into TF32 pairs: D = Xhi Rhi + Xhi Rlo + Xlo Rhi, which
+// carries the sum to about 2^-21 of its own size.  R_off is upper
+// triangular, so K atom k (orbitals 32k .. 32k+31) only feeds outputs
+// j >= 32k: its MMAs run with N = 128 - 32k and only those rows of R are
+// stored.  The tensor core adds into its FP32 accumulator with truncation (a
+// bias toward zero of a fraction of an ulp per accumulation), so the
+// dominant Xhi Rhi part is kept in two accumulators (atoms 0-1 and 2-3,
+// eight accumulations each), the small cross terms in a third, and the three
+// are added on the CUDA cores with round-to-nearest.  The self term R_jj x_j
+// is formed on the CUDA cores with a double-float R_jj and stored with
+// unbiased (dithered) rounding, because near convergence the corrections
+// that keep each orbital normalised are below half an ulp of its elements.
 //
-// With points on the lanes, every global access of the epilogue (w, hw of
-// the self term, the output, the density) is one 128-byte segment of one row
-// per warp instruction, and the density of a point is a per-thread sum.
+// The whole 128-point X tile stays in shared memory (four atom slots) until
+// the epilogue has used it: Xhi = tf32(x) and Xlo = x - Xhi (exact in FP32;
+// the tensor core reads its leading TF32 bits), so that x = Xhi + Xlo is
+// available to the self term without reading w and hw again.
+//
+// With points on the lanes, every global access of the epilogue (the output,
+// the density) is one 128-byte segment of one row per warp instruction, and
+// the density of a point is a per-thread sum.
 //
 // Pipeline per tile of 128 points (one CTA per SM, 512 threads: 16 warps,
 // four per SM sub-partition, so that each thread may hold 128 registers):
 //   warps 0-7   (producers) load one 32-orbital K atom of the tile at a time
-//               (eight lanes per 128-byte row segment), two atoms ahead so
-//               that each SM keeps two atoms of loads in flight, form Wt,
-//               split, and write it K-major (128-byte swizzle) into one of
-//               two atom slots; warp 0 also allocates tensor memory, and its
+//               (eight lanes per 128-byte row segment), two atoms ahead, form
+//               Wt, split it and write it K-major (128-byte swizzle) into the
+//               atom's slot once the previous tile's MMAs and epilogue are
+//               done with it; warp 0 also allocates tensor memory, and its
 //               lane 0 issues the MMAs of an atom once all producers wrote it;
 //   warps 8-15  (epilogue; two warps per TMEM lane quadrant, 64 output
 //               columns each) add the three accumulators into the 128 free
 //               tensor-memory columns and release them at once, so the next
-//               tile's MMAs overlap the rest: the self term (w and hw read in
-//               8-column groups, the next group's loads in flight while one
-//               is finished), the stores and the squares for the density.
+//               tile's MMAs overlap the rest: the self term from the resident
+//               X tile, the stores and the squares for the density; each
+//               warp frees an atom slot as soon as it has read its columns.
 // Tile rows are permuted within each 32-point group (row 8e + q holds point
 // 4q + e) so that the producers' transposing shared-memory stores hit 32
-// distinct banks.
+// distinct banks; the epilogue lane of a row is then row mod 32.
 #include "pou_internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -56,22 +64,28 @@ constexpr int EPI0 = PROD_WARPS;           // first epilogue warp
 constexpr int NTHR = (EPI0 + EPI_WARPS) * 32;
 constexpr int ATOM = 128 * 128;            // bytes of one K atom: 128 rows x 128 bytes
 constexpr int SLOT = 2 * ATOM;             // one X atom: hi rows, then lo rows
-constexpr int OFF_RHI = 0;                 // R_off as the B operand: rows j, K = i
-constexpr int OFF_RLO = OFF_RHI + 4 * ATOM;
-constexpr int OFF_X = OFF_RLO + 4 * ATOM;  // two X atom slots
-constexpr int OFF_SELF = OFF_X + 2 * SLOT;         // 128 x float4 (A_hi, A_lo, B_hi, B_lo)
-constexpr int OFF_COEF = OFF_SELF + 4 * 128 * 4;   // 128 floats
-constexpr int OFF_DENS = OFF_COEF + 128 * 4;       // [4 quadrants][32] x (s, c)
+// R_off as the B operand, rows j >= 32 k of atom k (K = i): 128, 96, 64, 32 rows
+__host__ __device__ constexpr int r_rows(int k) { return 128 - 32 * k; }
+__host__ __device__ constexpr int r_row0(int k) { return 128 * k - 16 * k * (k - 1); }
+constexpr int R_BYTES = 128 * (128 + 96 + 64 + 32);
+constexpr int OFF_RHI = 0;
+constexpr int OFF_RLO = OFF_RHI + R_BYTES;
+constexpr int OFF_X = OFF_RLO + R_BYTES;           // four X atom slots (one tile)
+constexpr int OFF_SELF = OFF_X + 4 * SLOT;         // 128 x float2: R_jj as (hi, lo)
+constexpr int OFF_COEF = OFF_SELF + 128 * 8;       // 128 x float2: 1 + tau sigma_i as (hi, lo)
+constexpr int OFF_DENS = OFF_COEF + 128 * 8;       // [4 quadrants][32] x (s, c)
 constexpr int OFF_BAR = OFF_DENS + 4 * 32 * 8;
-// barriers: full[2], empty[2], accf, acce, fin; then tmem slot, abort flag
-constexpr int NBAR = 7;
+// barriers: full[4], empty[4], accf, acce, fin; then tmem slot, abort flag
+constexpr int NBAR = 11;
 constexpr int OFF_MISC = OFF_BAR + NBAR * 8;
 constexpr int SMEM_BYTES = OFF_MISC + 16 + 1024;  // + alignment slack
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t COL_HH1 = 128, COL_X = 256;   // accumulators: hh0 at 0, hh1, cross terms
 constexpr uint32_t COL_OFF = 384;                // epilogue copy of the summed accumulators
-constexpr uint32_t IDESC = tc::idesc_tf32(128, 128);
+// the empty barrier of a slot: the MMA commit and the four epilogue warps reading its columns
+constexpr int EMPTY_ARRIVALS = 1 + 4;
 
+static_assert(OFF_RLO % 1024 == 0 && OFF_X % 1024 == 0, "swizzled tiles need 1024-byte alignment");
 static_assert(SMEM_BYTES <= 232448, "tensor-core rotation exceeds the shared-memory opt-in limit");
 
 __device__ unsigned int g_rotate_tc_aborts = 0;
@@ -112,13 +126,13 @@ __global__ void __launch_bounds__(NTHR, 1) k_rotate_tc(RotArgs<float> a, i64 nti
   const uint32_t pad = (1024u - (raw_addr & 1023u)) & 1023u;
   unsigned char* smem = smem_raw + pad;
   const uint32_t sbase = raw_addr + pad;
-  float4* self = reinterpret_cast<float4*>(smem + OFF_SELF);  // (A_hi, A_lo, B_hi, B_lo) per orbital
+  float2* self = reinterpret_cast<float2*>(smem + OFF_SELF);  // R_jj as (hi, lo)
   float2* dens = reinterpret_cast<float2*>(smem + OFF_DENS);
-  float* coefs = reinterpret_cast<float*>(smem + OFF_COEF);
+  float2* coefs = reinterpret_cast<float2*>(smem + OFF_COEF);
   const uint32_t bar0 = sbase + OFF_BAR;
   auto full_bar = [&](int k) { return bar0 + 8u * k; };
-  auto empty_bar = [&](int k) { return bar0 + 8u * (2 + k); };
-  const uint32_t accf_bar = bar0 + 32u, acce_bar = bar0 + 40u, fin_bar = bar0 + 48u;
+  auto empty_bar = [&](int k) { return bar0 + 8u * (4 + k); };
+  const uint32_t accf_bar = bar0 + 64u, acce_bar = bar0 + 72u, fin_bar = bar0 + 80u;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + OFF_MISC);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + OFF_MISC + 4);
 
@@ -156,39 +170,38 @@ __global__ void __launch_bounds__(NTHR, 1) k_rotate_tc(RotArgs<float> a, i64 nti
     out = a.B;
     rho = a.rho_out;
   }
-  const float tauF = (float)tau;
+  const float tauH = (float)tau, tauL = (float)(tau - (double)tauH);
 
-  // B operand = off-diagonal R (row j, K index i) split into TF32 pairs, the
-  // self-term coefficients, and the trial coefficients 1 + tau sigma_i
-  for (int idx = tid; idx < 128 * 128; idx += NTHR) {
-    const int i = idx >> 7, j = idx & 127;
+  // B operand = strictly upper R (row j, K index i) split into TF32 pairs,
+  // rows j >= 32 k of atom k only; the self-term coefficients R_jj; the
+  // trial coefficients 1 + tau sigma_i
+  for (int idx = tid; idx < 320 * 32; idx += NTHR) {
+    const int row = idx >> 5, il = idx & 31;  // stored row, K index within the atom
+    const int k = row < 128 ? 0 : (row < 224 ? 1 : (row < 288 ? 2 : 3));
+    const int r = row - r_row0(k);           // j - 32 k
+    const int i = 32 * k + il, j = 32 * k + r;
     double v = 0.0;
-    if (i < N && j < N && i != j && (a.general || i < j)) v = a.Rinv[(i64)i * N + j];
+    if (i < j && j < N) v = a.Rinv[(i64)i * N + j];
     const float hi = tc::to_tf32((float)v);
     const float lo = tc::to_tf32((float)(v - (double)hi));
-    const int off = (i >> 5) * ATOM + j * 128 + ((((i & 31) >> 2) ^ (j & 7)) << 4) + (i & 3) * 4;
+    const int off = row * 128 + (((il >> 2) ^ (r & 7)) << 4) + (il & 3) * 4;
     *reinterpret_cast<float*>(smem + OFF_RHI + off) = hi;
     *reinterpret_cast<float*>(smem + OFF_RLO + off) = lo;
   }
   for (int j = tid; j < 128; j += NTHR) {
-    double A = 0.0, B = 0.0, cf = 1.0;
+    double A = 0.0, cf = 1.0;
     if (j < N) {
-      const double v = a.Rinv[(i64)j * N + j];
-      A = v;
-      if (a.trial) {
-        cf = 1.0 + tau * a.sigma[cur][j];
-        A = v * cf;
-        B = v * tau;
-      }
+      A = a.Rinv[(i64)j * N + j];
+      if (a.trial) cf = 1.0 + tau * a.sigma[cur][j];
     }
-    const float ah = (float)A, bh = (float)B;
-    self[j] = make_float4(ah, (float)(A - (double)ah), bh, (float)(B - (double)bh));
-    coefs[j] = (float)cf;
+    const float ah = (float)A, ch = (float)cf;
+    self[j] = make_float2(ah, (float)(A - (double)ah));
+    coefs[j] = make_float2(ch, (float)(cf - (double)ch));
   }
   if (tid == 0) {
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 4; ++k) {
       tc::mbar_init(full_bar(k), PROD_WARPS * 32);
-      tc::mbar_init(empty_bar(k), 1);
+      tc::mbar_init(empty_bar(k), EMPTY_ARRIVALS);
     }
     tc::mbar_init(accf_bar, 1);
     tc::mbar_init(acce_bar, EPI_WARPS * 32);
@@ -253,55 +266,59 @@ __global__ void __launch_bounds__(NTHR, 1) k_rotate_tc(RotArgs<float> a, i64 nti
     };
     bool issued = false;
     // one atom: loads for atom u + 2 go into the register set that held
-    // atom u - 1; atom u is written from (w, h)
+    // atom u - 1; atom u is written from (w, h) into slot u % 4
     auto step = [&](int u, const float4 (&w)[4], const float4 (&h)[4], float4 (&wl)[4], float4 (&hl)[4]) -> bool {
       if (u + 2 < natoms) issue(u + 2, wl, hl);
-      const int k = u & 3, slot = u & 1, n = u >> 1;
-      if (n > 0 && !tc::mbar_wait(empty_bar(slot), (n - 1) & 1, abort_flag)) return false;
-      unsigned char* xs = smem + OFF_X + slot * SLOT;
-      const float cf = coefs[32 * k + 4 * warp + isub];
+      const int k = u & 3, t = u >> 2;
+      // the previous tile's MMAs and epilogue are done with the slot
+      if (t > 0 && !tc::mbar_wait(empty_bar(k), (t - 1) & 1, abort_flag)) return false;
+      unsigned char* xs = smem + OFF_X + k * SLOT;
+      const float2 cf = coefs[32 * k + 4 * warp + isub];
 #pragma unroll
       for (int g = 0; g < 4; ++g) {
-        float x[4] = {w[g].x, w[g].y, w[g].z, w[g].w};
-        if (Hsrc) {
-          const float h4[4] = {h[g].x, h[g].y, h[g].z, h[g].w};
-#pragma unroll
-          for (int e = 0; e < 4; ++e) x[e] = cf * x[e] - tauF * h4[e];
-        }
+        const float x[4] = {w[g].x, w[g].y, w[g].z, w[g].w};
+        const float h4[4] = {h[g].x, h[g].y, h[g].z, h[g].w};
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const int row = 32 * g + 8 * e + q;  // holds point 32 g + 4 q + e; row % 8 == q
-          const float hi = tc::to_tf32(x[e]);
-          const float lo = tc::to_tf32(x[e] - hi);
+          float hi, lo;
+          if (Hsrc) {
+            tc::trial_split(cf.x, cf.y, x[e], tauH, tauL, h4[e], hi, lo);
+          } else {
+            hi = tc::to_tf32(x[e]);
+            lo = x[e] - hi;  // exact
+          }
           const int off = row * 128 + ((warp ^ q) << 4) + isub * 4;
           *reinterpret_cast<float*>(xs + off) = hi;
           *reinterpret_cast<float*>(xs + ATOM + off) = lo;
         }
       }
       tc::fence_proxy_async_smem();
-      tc::mbar_arrive(full_bar(slot));
+      tc::mbar_arrive(full_bar(k));
       if (warp == 0) {
         // ---------------------------------------------------- MMA issue
         int ok = 1;
         if (lane == 0) {
-          const int t = u >> 2;
           if (k == 0 && t > 0) ok = tc::mbar_wait(acce_bar, (t - 1) & 1, abort_flag);
-          if (ok) ok = tc::mbar_wait(full_bar(slot), n & 1, abort_flag);
+          if (ok) ok = tc::mbar_wait(full_bar(k), t & 1, abort_flag);
           if (ok) {
             tc::fence_after_sync();
-            const uint32_t xh = sbase + OFF_X + slot * SLOT, xl = xh + ATOM;
-            const uint32_t rh = sbase + OFF_RHI + k * ATOM, rl = sbase + OFF_RLO + k * ATOM;
-            const uint32_t dhh = tmem + ((k >> 1) ? COL_HH1 : 0u), dx = tmem + COL_X;
+            const uint32_t xh = sbase + OFF_X + k * SLOT, xl = xh + ATOM;
+            const uint32_t rh = sbase + OFF_RHI + r_row0(k) * 128, rl = sbase + OFF_RLO + r_row0(k) * 128;
+            // outputs j >= 32 k only: columns 32 k .. 127, N = 128 - 32 k
+            const uint32_t c0 = 32u * k;
+            const uint32_t dhh = tmem + ((k >> 1) ? COL_HH1 : 0u) + c0, dx = tmem + COL_X + c0;
+            const uint32_t idesc = tc::idesc_tf32(128, r_rows(k));
 #pragma unroll
             for (int s4 = 0; s4 < 4; ++s4) {
               const uint64_t axh = tc::desc_sw128(xh + 32u * s4), axl = tc::desc_sw128(xl + 32u * s4);
               const uint64_t brh = tc::desc_sw128(rh + 32u * s4), brl = tc::desc_sw128(rl + 32u * s4);
-              tc::mma_tf32(dhh, axh, brh, IDESC, ((k & 1) == 0 && s4 == 0) ? 0u : 1u);
-              tc::mma_tf32(dx, axh, brl, IDESC, (k == 0 && s4 == 0) ? 0u : 1u);
-              tc::mma_tf32(dx, axl, brh, IDESC, 1u);
+              tc::mma_tf32(dhh, axh, brh, idesc, ((k & 1) == 0 && s4 == 0) ? 0u : 1u);
+              tc::mma_tf32(dx, axh, brl, idesc, (k == 0 && s4 == 0) ? 0u : 1u);
+              tc::mma_tf32(dx, axl, brh, idesc, 1u);
             }
             issued = true;
-            tc::mma_commit(empty_bar(slot));
+            tc::mma_commit(empty_bar(k));
             if (k == 3) tc::mma_commit(accf_bar);
           }
         }
@@ -331,39 +348,40 @@ __global__ void __launch_bounds__(NTHR, 1) k_rotate_tc(RotArgs<float> a, i64 nti
     const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
     const uint32_t off_col = COL_OFF + (uint32_t)(64 * jh);  // this warp's copy of its 64 sums
     const unsigned seed32 = mix32((unsigned)(a.st ? a.st->passes : 0) * 4u + (unsigned)a.sr_salt + 0x85ebca6bu);
-    // w and hw of one 8-column group for this lane's point
-    auto fetch = [&](i64 p, int g, float (&wv)[8], float (&hv)[8]) {
-#pragma unroll
-      for (int m = 0; m < 8; ++m) {
-        const int j = 64 * jh + 8 * g + m;
-        wv[m] = hv[m] = 0.f;
-        if (p < ng && j < N) {
-          wv[m] = Wsrc[(i64)j * ng + p];
-          if (Hsrc) hv[m] = Hsrc[(i64)j * ng + p];
-        }
-      }
-    };
+    // this lane's tile row in the X slots (row 32 quad + lane holds point pt)
+    const int row = 32 * quad + lane;
     // density of this lane's point over the 64 columns: four independent
     // double-float chains (one per column mod 4), so that the compensated
     // additions do not form one serial dependency
     float rs[4], rc[4];
     // one 8-column group: self term, dithered rounding, store, squares
-    auto finish = [&](i64 p, int g, const float (&wv)[8], const float (&hv)[8]) {
+    auto finish = [&](i64 p, int g) {
       uint32_t ov[8];
       tc::tmem_ld8(lane_base + off_col + (uint32_t)(8 * g), ov);
+      const int j0 = 64 * jh + 8 * g;
+      const unsigned char* xs = smem + OFF_X + (j0 >> 5) * SLOT;
+      float xh[8], xl[8];  // x = xh + xl
+#pragma unroll
+      for (int h4 = 0; h4 < 2; ++h4) {
+        const int chunk = ((j0 & 31) >> 2) + h4;
+        const int off = row * 128 + ((chunk ^ (row & 7)) << 4);
+        const float4 vh = *reinterpret_cast<const float4*>(xs + off);
+        const float4 vl = *reinterpret_cast<const float4*>(xs + ATOM + off);
+        xh[4 * h4 + 0] = vh.x, xh[4 * h4 + 1] = vh.y, xh[4 * h4 + 2] = vh.z, xh[4 * h4 + 3] = vh.w;
+        xl[4 * h4 + 0] = vl.x, xl[4 * h4 + 1] = vl.y, xl[4 * h4 + 2] = vl.z, xl[4 * h4 + 3] = vl.w;
+      }
       tc::tmem_wait_ld();
 #pragma unroll
       for (int m4 = 0; m4 < 8; m4 += 4) {
         // one 32-bit draw per (4 columns, point): one byte per element
-        const unsigned bits =
-            mix32(seed32 ^ mix32((unsigned)((64 * jh + 8 * g + m4) >> 2) * 0x9e3779b1u ^ (unsigned)p));
+        const unsigned bits = mix32(seed32 ^ mix32((unsigned)((j0 + m4) >> 2) * 0x9e3779b1u ^ (unsigned)p));
 #pragma unroll
         for (int m = m4; m < m4 + 4; ++m) {
-          const int j = 64 * jh + 8 * g + m;
-          const float4 c = self[j];  // A_hi, A_lo, B_hi, B_lo
-          const float d = dither(wv[m], (bits >> (8 * (m - m4))) & 0xffu);
-          const float rest = fmaf(c.y, wv[m], fmaf(-c.w, hv[m], __uint_as_float(ov[m]) + d));
-          const float o = fmaf(c.x, wv[m], fmaf(-c.z, hv[m], rest));
+          const int j = j0 + m;
+          const float2 c = self[j];  // R_jj (hi, lo)
+          const float d = dither(xh[m], (bits >> (8 * (m - m4))) & 0xffu);
+          // R_jj x = (c.x + c.y)(xh + xl), one rounding at the output's scale
+          const float o = fmaf(c.x, xh[m], fmaf(c.x, xl[m], fmaf(c.y, xh[m], __uint_as_float(ov[m]) + d)));
           if (p < ng && j < N) {
             out[(i64)j * ng + p] = o;
             const float sq = o * o;
@@ -372,24 +390,28 @@ __global__ void __launch_bounds__(NTHR, 1) k_rotate_tc(RotArgs<float> a, i64 nti
         }
       }
     };
-    float wA[8], hA[8], wB[8], hB[8];
-    if (nmine > 0) fetch(t0 * TPTS + pt, 0, wA, hA);
     for (int t = 0; t < nmine; ++t) {
       const i64 p = (t0 + t) * TPTS + pt;
       if (!tc::mbar_wait(accf_bar, t & 1, abort_flag)) break;
       tc::fence_after_sync();
-      // off-diagonal sums: the three accumulators added and copied to this
-      // warp's free tensor-memory columns, then released
+      // off-diagonal sums: the accumulators added and copied to this warp's
+      // free tensor-memory columns, then released (outputs j < 64 receive
+      // nothing from atoms 2-3: the hh1 columns 0..63 are never written)
 #pragma unroll 1
       for (int c = 0; c < 64; c += 16) {
         uint32_t h0[16], h1[16], xx[16];
         tc::tmem_ld16(lane_base + (uint32_t)(64 * jh + c), h0);
-        tc::tmem_ld16(lane_base + COL_HH1 + (uint32_t)(64 * jh + c), h1);
+        if (jh) tc::tmem_ld16(lane_base + COL_HH1 + (uint32_t)(64 * jh + c), h1);
         tc::tmem_ld16(lane_base + COL_X + (uint32_t)(64 * jh + c), xx);
         tc::tmem_wait_ld();
+        if (jh) {
 #pragma unroll
-        for (int m = 0; m < 16; ++m)
-          h0[m] = __float_as_uint((__uint_as_float(h0[m]) + __uint_as_float(h1[m])) + __uint_as_float(xx[m]));
+          for (int m = 0; m < 16; ++m)
+            h0[m] = __float_as_uint((__uint_as_float(h0[m]) + __uint_as_float(h1[m])) + __uint_as_float(xx[m]));
+        } else {
+#pragma unroll
+          for (int m = 0; m < 16; ++m) h0[m] = __float_as_uint(__uint_as_float(h0[m]) + __uint_as_float(xx[m]));
+        }
         tc::tmem_st16(lane_base + off_col + (uint32_t)c, h0);
       }
       tc::tmem_wait_st();
@@ -398,16 +420,14 @@ __global__ void __launch_bounds__(NTHR, 1) k_rotate_tc(RotArgs<float> a, i64 nti
 
 #pragma unroll
       for (int c = 0; c < 4; ++c) rs[c] = rc[c] = 0.f;
-      // groups 0..7, the next group's loads in flight while one is finished
 #pragma unroll 1
-      for (int g = 0; g < 8; g += 2) {
-        fetch(p, g + 1, wB, hB);
-        finish(p, g, wA, hA);
-        if (g + 2 < 8)
-          fetch(p, g + 2, wA, hA);
-        else if (t + 1 < nmine)
-          fetch(p + TPTS, 0, wA, hA);
-        finish(p, g + 1, wB, hB);
+      for (int g = 0; g < 8; ++g) {
+        finish(p, g);
+        if ((g & 3) == 3) {
+          // this warp has read its columns of atom 2 jh + g / 4
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(empty_bar(2 * jh + (g >> 2)));
+        }
       }
       f2_add(rs[0], rc[0], rs[1], rc[1]);
       f2_add(rs[2], rc[2], rs[3], rc[3]);

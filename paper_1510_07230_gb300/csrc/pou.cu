@@ -348,6 +348,7 @@ void enqueue_diag(pou_ctx* c) {
   launch_apply_h<T>(aa, c->cfg.stencil_order, s, &ntile);
   CtrlArgs k{};
   k.st = c->st;
+  k.fp32 = c->dt == 1 ? 1 : 0;
   for (int q = 0; q < 2; ++q) {
     k.sigma[q] = c->sigma[q];
     k.part[q] = c->part[q];
@@ -394,12 +395,17 @@ void enqueue_pass(pou_ctx* c) {
   r.general = 0;
   r.dV = c->dV;
   r.S = c->S;
+  // Diagonal of the trial Gram matrix: the squared norm of the very column
+  // the rotation scales by R_jj.  Both rotations form the trial point with
+  // the FP64 coefficients (the FP32 one as a double-float, hi + lo), so the
+  // diagonal is the FP64 norm of (1 + tau sigma) w - tau hw from the
+  // H-apply sums.
   r.trial = 1;
   for (int k = 0; k < 2; ++k) {
     r.sigma[k] = c->sigma[k];
     r.part[k] = c->part[k];
   }
-  r.fp32_coef = 0;  // the rotation's self term uses the FP64 coefficients
+  r.fp32_coef = 0;
   launch_gram_reduce(r, s);
   // Cholesky and R^-1 in FP64
   launch_cholinv(c->st, c->S, c->Rinv, c->N, nullptr, c->st, pivot_tol(c), reorth_thr(c), s);
@@ -459,6 +465,7 @@ void enqueue_pass(pou_ctx* c) {
   // accept / reject
   CtrlArgs k{};
   k.st = c->st;
+  k.fp32 = c->dt == 1 ? 1 : 0;
   k.hist_E = c->hist_E;
   k.hist_tau = c->hist_tau;
   for (int q = 0; q < 2; ++q) {
@@ -561,6 +568,7 @@ pou_status init_from_staged(pou_ctx* c) {
   launch_apply_h<T>(aa, c->cfg.stencil_order, s, &ntile);
   CtrlArgs k{};
   k.st = c->st;
+  k.fp32 = c->dt == 1 ? 1 : 0;
   k.hist_E = c->hist_E;
   k.hist_tau = c->hist_tau;
   for (int q = 0; q < 2; ++q) {

@@ -245,6 +245,7 @@ struct CtrlArgs {
   int bb_variant, max_backtrack;
   int n_diag;           // subspace diagonalisation period (0: off)
   int refresh;          // 1: re-reduce the sums of the rotated current pair only
+  int fp32;             // the H-apply formed z' = hw - sigma' w with sigma' rounded to FP32
   double kc[3];         // kinetic coefficient per axis: -1/2 * (1 or 1/12) / h_a^2
 };
 void launch_control(const CtrlArgs& a, cudaStream_t s);

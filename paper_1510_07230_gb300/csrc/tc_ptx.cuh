@@ -200,5 +200,27 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(r);
 }
 
+// Trial point of the FP32 form, x = a w - t hw with a = 1 + tau sigma_i and
+// t = tau (Sec. 3.2), from FP64 coefficients given as float pairs
+// (a = ah + al, t = th + tl), returned split for the tensor cores:
+// hi = tf32(x) and lo = x - hi rounded to FP32, so that hi + lo carries x to
+// about 2^-35 of its size and a step smaller than half an FP32 ulp of w is
+// not rounded away.  The two products are formed exactly (FMA) and added
+// with TwoSum (Knuth); every operation is spelled out, so that the Gram
+// matrix and the rotation of a trial see bit-identical values.
+__device__ __forceinline__ void trial_split(float ah, float al, float w, float th, float tl, float hw, float& hi,
+                                            float& lo) {
+  const float m = __fmul_rn(ah, w);
+  const float me = __fmaf_rn(ah, w, -m);
+  const float p = __fmul_rn(th, hw);
+  const float pe = __fmaf_rn(th, hw, -p);
+  const float s = __fsub_rn(m, p);
+  const float b = __fsub_rn(s, m);
+  const float se = __fadd_rn(__fsub_rn(m, __fsub_rn(s, b)), __fsub_rn(-p, b));
+  const float tail = __fadd_rn(__fsub_rn(__fadd_rn(se, me), pe), __fmaf_rn(al, w, -__fmul_rn(tl, hw)));
+  hi = to_tf32(s);
+  lo = __fadd_rn(__fsub_rn(s, hi), tail);
+}
+
 }  // namespace tc
 }  // namespace pou
