@@ -95,7 +95,8 @@ typedef struct {
   void* stream;       /* cudaStream_t to run on; NULL: the library creates one */
 } pou_config;
 
-#define POU_MAX_N 128
+#define POU_MAX_N 512      /* FP32 form (without the subspace diagonalisation) */
+#define POU_MAX_N_FP64 128 /* FP64 form, the subspace diagonalisation, pou_gradient_norm, FP64 pou_rotate */
 
 typedef struct {
   double kinetic;   /* f sum_i <w_i, -1/2 Lap_h w_i> */
@@ -175,7 +176,8 @@ pou_status pou_get_potential(pou_ctx* ctx, double* V, int on_device);
  * (host).  Sigma is formed on the device in the working precision; G is
  * formed point by point and its squares summed in FP64.  Synchronises the
  * context's stream.  POU_EINVAL when no orbitals are set.  Overwrites the
- * context's N x N scratch matrix (not part of the iteration state). */
+ * context's N x N scratch matrix (not part of the iteration state).  N <= POU_MAX_N_FP64
+ * (POU_EINVAL above). */
 pou_status pou_gradient_norm(pou_ctx* ctx, double* out);
 
 /* Energy of an arbitrary block U (not orthonormalised, Eq. energy) without
@@ -230,8 +232,8 @@ pou_status pou_get_profile(pou_ctx* ctx, int max_entries, char* names, long long
  * ------------------------------------------------------------------------ */
 
 /* Gram matrix S = dV * A^T A (Sec. 3.2, Cholesky-based QR, first step) of a
- * block A of N columns of length Ng, stored [N][Ng] in dtype.  S: N*N device
- * doubles, row-major and symmetric.  workspace: device memory of at least
+ * block A of N <= POU_MAX_N columns of length Ng, stored [N][Ng] in dtype.
+ * S: N*N device doubles, row-major and symmetric.  workspace: device memory of at least
  * pou_gram_workspace_bytes(dtype, Ng, N) bytes, 256-byte aligned. */
 size_t pou_gram_workspace_bytes(int dtype, long long Ng, int N);
 pou_status pou_gram(int dtype, long long Ng, int N, const void* A, double dV, double* S,
@@ -261,14 +263,19 @@ pou_status pou_gram_noalloc(int dtype, long long Ng, int N, const void* A, doubl
 
 /* Cholesky factor and triangular inverse (Sec. 3.2): S = R^T R with R upper
  * triangular and positive diagonal, Rinv = R^-1 (N*N device doubles,
- * row-major, lower part zero).  *info (device int) is 0 on success or k+1 if
- * the k-th pivot is not positive (then Rinv is unspecified). */
+ * row-major, lower part zero), N <= POU_MAX_N.  *info (device int) is 0 on
+ * success or k+1 if the k-th pivot is not positive (then Rinv is
+ * unspecified).  For N > 128 Rinv also serves as the working matrix and the
+ * call is a sequence of kernels on the stream. */
 pou_status pou_cholinv(int N, const double* S, double* Rinv, int* info, void* stream);
 
 /* Rotation and density (Sec. 3.2 Orth, last step; Sec. 2.1 density):
  * B = A Rinv (columns), i.e. B_j = sum_{i<=j} Rinv[i][j] A_i, and
- * rho = f sum_j B_j^2 (FP64).  A, B: [N][Ng] dtype; Rinv: N*N doubles;
- * rho: Ng doubles (may be NULL). */
+ * rho = f sum_j B_j^2 (FP64).  A, B: [N][Ng] dtype; Rinv: N*N doubles, upper
+ * triangular; rho: Ng doubles (may be NULL).  N <= POU_MAX_N for FP32,
+ * N <= POU_MAX_N_FP64 for FP64.  FP32 with N > 128 takes a stream-ordered
+ * scratch of a few MB (cudaMallocAsync), released on the same stream;
+ * POU_ENOMEM if it cannot be had. */
 pou_status pou_rotate(int dtype, long long Ng, int N, const void* A, const double* Rinv,
                       void* B, double* rho, void* stream);
 

@@ -665,8 +665,8 @@ void gram_layout(i64 ng, int N, bool general, int* nsplit, int* npair, i64* chun
   const int nsup = (N + ST - 1) / ST;
   const int np = general ? nsup * nsup : nsup * (nsup + 1) / 2;
   const i64 ntiles = (ng + BK - 1) / BK;
-  // one CTA per SM in total, at least 32 tiles per CTA
-  i64 g = (152 + np - 1) / np;
+  // one CTA per SM in total (one wave), at least 32 tiles per CTA
+  i64 g = std::max(1, 152 / np);
   g = std::max<i64>(1, std::min<i64>(g, ntiles / 32));
   *npair = np;
   *chunk = ntiles;  // tiles over the whole grid

@@ -1,16 +1,26 @@
 // Gram matrix of the FP32 form on the 5th-generation tensor cores
 // (Cholesky-QR, Sec. 3.2: S = <Wt^T Wt> of the trial block
 // Wt = (1 + tau sigma_i) w_i - tau hw_i, of the second-pass block, or of a
-// caller's block), for N <= 128 orbitals.
+// caller's block), for N <= 512 orbitals.
+//
+// The N x N matrix is cut into 128 x 128 blocks (I, J), I <= J; each CTA
+// computes one block over one range of grid points, and the CTAs of one
+// range are launched side by side, so that the rows they share are read
+// from HBM about once.  A diagonal block streams its 128 rows; an
+// off-diagonal block alternates tiles of rows I and rows J of the same 32
+// points through the ring, so that every producer thread still holds four
+// rows of one block at a time.
 //
 // Precision: every FP32 value x of the block is split into hi = tf32(x) and
 // lo = x - hi (exact in FP32); the tensor core reads the leading TF32 bits of
 // lo (truncation), so x = hi + lo + O(2^-22 x), the same split the
-// tensor-core rotation applies to the block it rotates.  Per K step two
-// MMAs of shape M = N = 128, K = 8 accumulate D += Hi Hi^T + Hi (2 Lo)^T, so
-// that the symmetric part (D + D^T) / 2 = Hi Hi^T + Hi Lo^T + Lo Hi^T is the
-// Gram to about 2^-21 relative per product (random sign); the reduction
-// kernel takes that symmetric part.  The tensor core adds into its FP32
+// tensor-core rotation applies to the block it rotates.  On a diagonal block
+// two MMAs of shape M = N = 128, K = 8 per K step accumulate
+// D += Hi Hi^T + Hi (2 Lo)^T, so that the symmetric part
+// (D + D^T) / 2 = Hi Hi^T + Hi Lo^T + Lo Hi^T is the Gram to about 2^-21
+// relative per product (random sign); the reduction kernel takes that
+// symmetric part.  An off-diagonal block takes the three products
+// D += Jhi Ihi^T + Jhi Ilo^T + Jlo Ihi^T.  The tensor core adds into its FP32
 // accumulator with truncation, which biases long sums toward zero, so the
 // accumulator is restarted every PERIOD stages (64 grid points) and each
 // partial is added into a compensated pair (sum, error) that also lives in
@@ -56,7 +66,8 @@ constexpr int OFF_BAR = OFF_DIAG + 128 * 8;
 constexpr int NBAR = 2 * STAGES + 5;
 constexpr int OFF_MISC = OFF_BAR + NBAR * 8;
 constexpr int OFF_COEF = OFF_MISC + 16;
-constexpr int SMEM_BYTES = OFF_COEF + 128 * 8 + 1024;  // + alignment slack
+constexpr int MAXN = 512;            // orbitals: at most four 128-row blocks
+constexpr int SMEM_BYTES = OFF_COEF + MAXN * 8 + 1024;  // + alignment slack
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t COL_SUM = 256, COL_ERR = 384;
 constexpr uint32_t IDESC = tc::idesc_tf32(128, 128);
@@ -103,10 +114,20 @@ __global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb)
   const int N = a.N;
   const i64 ng = a.ng;
 
-  // this CTA's contiguous range of stages
-  const i64 G = gridDim.x;
-  const i64 kb0 = nkb * (i64)blockIdx.x / G, kb1 = nkb * (i64)(blockIdx.x + 1) / G;
-  const int nmine = (int)(kb1 - kb0);
+  // block pair (I, J) of this CTA and its contiguous range of 32-point
+  // chunks: CTA = split * npair + pair, pairs in upper row-major order
+  const int nsup = (N + 127) / 128, npair = nsup * (nsup + 1) / 2;
+  const int pair = (int)(blockIdx.x % npair);
+  const i64 split = blockIdx.x / npair, G = gridDim.x / npair;
+  int I = 0, J = 0;
+  for (int p = pair; p >= nsup - I; p -= nsup - I, ++I) {
+  }
+  J = I + (pair - (I * nsup - I * (I - 1) / 2));
+  const bool offd = I != J;
+  const i64 kb0 = nkb * split / G, kb1 = nkb * (split + 1) / G;
+  // steps: one 128-row tile each; an off-diagonal block takes the I and the
+  // J tile of every chunk in turn
+  const int nmine = (int)(kb1 - kb0) * (offd ? 2 : 1);
   const int nper = (nmine + PERIOD - 1) / PERIOD;
 
   const float* Wa;
@@ -119,7 +140,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb)
     const double tau = a.st->tau_trial;
     tauH = (float)tau;
     tauL = (float)(tau - (double)tauH);
-    for (int r = tid; r < 128; r += NTHR) {
+    for (int r = tid; r < MAXN; r += NTHR) {
       const double cf = r < N ? 1.0 + tau * a.sigma[cur][r] : 0.0;
       const float ch = (float)cf;
       coefs[r] = make_float2(ch, (float)(cf - (double)ch));
@@ -158,11 +179,15 @@ __global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb)
     const int c = pt & 7;         // 16-byte chunk of the row: points 4c .. 4c+3
     const int r0 = pt >> 3;       // rows r0 + 32 q
     float ds[4] = {0.f, 0.f, 0.f, 0.f}, dc[4] = {0.f, 0.f, 0.f, 0.f};  // diagonal, double-float
-    auto load = [&](i64 kb, float4 (&wv)[4], float4 (&hv)[4]) {
+    // step i: chunk kb0 + i (diagonal) or kb0 + i / 2, rows of block I or J
+    auto rbase = [&](int i) { return 128 * ((offd && (i & 1)) ? J : I); };
+    auto load = [&](int i, float4 (&wv)[4], float4 (&hv)[4]) {
+      const i64 kb = kb0 + (offd ? (i >> 1) : i);
+      const int rb = rbase(i);
       const i64 p = kb * KB + 4 * c;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int r = r0 + 32 * q;
+        const int r = rb + r0 + 32 * q;
         wv[q] = make_float4(0.f, 0.f, 0.f, 0.f);
         hv[q] = wv[q];
         if (r >= N) continue;
@@ -188,31 +213,34 @@ __global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb)
     };
     // one stage: loads for stage i + 2 go into the register set that held
     // stage i - 1; stage i is written from (w, h)
+    // lo is stored doubled for the symmetric two-product form of a diagonal block
+    const float lo_scale = offd ? 1.0f : 2.0f;
     auto step = [&](int i, const float4 (&w)[4], const float4 (&h)[4], float4 (&wl)[4], float4 (&hl)[4]) -> bool {
-      if (i + 2 < nmine) load(kb0 + i + 2, wl, hl);
+      if (i + 2 < nmine) load(i + 2, wl, hl);
       const int s = i % STAGES, n = i / STAGES;
       if (n > 0 && !tc::mbar_wait(empty_bar(s), (n - 1) & 1, abort_flag)) return false;
       unsigned char* hi_t = smem + s * STAGE_BYTES;
       unsigned char* lo_t = hi_t + TILE;
+      const int rb = rbase(i);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int r = r0 + 32 * q;
+        const int r = r0 + 32 * q;  // row within the tile
         const float x[4] = {w[q].x, w[q].y, w[q].z, w[q].w};
         float hi[4], lo[4];
         if (TRIAL) {
-          const float2 cf = coefs[r];
+          const float2 cf = coefs[rb + r];
           const float hv4[4] = {h[q].x, h[q].y, h[q].z, h[q].w};
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             tc::trial_split(cf.x, cf.y, x[e], tauH, tauL, hv4[e], hi[e], lo[e]);
-            lo[e] *= 2.0f;
+            lo[e] *= lo_scale;
           }
         } else {
           float sq = 0.f;
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             hi[e] = tc::to_tf32(x[e]);
-            lo[e] = 2.0f * (x[e] - hi[e]);  // exact; the tensor core reads its leading TF32 bits
+            lo[e] = lo_scale * (x[e] - hi[e]);  // exact; the tensor core reads its leading TF32 bits
             sq = fmaf(x[e], x[e], sq);
           }
           two_sum_into(ds[q], dc[q], sq);
@@ -226,14 +254,15 @@ __global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb)
       return true;
     };
     float4 wA[4], hA[4], wB[4], hB[4], wC[4], hC[4];
-    if (nmine > 0) load(kb0, wA, hA);
-    if (nmine > 1) load(kb0 + 1, wB, hB);
+    if (nmine > 0) load(0, wA, hA);
+    if (nmine > 1) load(1, wB, hB);
     for (int i = 0; i < nmine; i += 3) {
       if (!step(i, wA, hA, wC, hC)) break;
       if (i + 1 >= nmine || !step(i + 1, wB, hB, wA, hA)) break;
       if (i + 2 >= nmine || !step(i + 2, wC, hC, wB, hB)) break;
     }
-    // the eight lanes that share a row hold its diagonal in parts
+    // the eight lanes that share a row hold its diagonal in parts (the sums
+    // of an off-diagonal block are not used)
 #pragma unroll
     for (int q = 0; q < (TRIAL ? 0 : 4); ++q) {
 #pragma unroll
@@ -255,6 +284,33 @@ __global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb)
         if (use > 0 && !tc::mbar_wait(acce_bar(b), (use - 1) & 1, abort_flag)) break;
         tc::fence_after_sync();
         const uint32_t d = tmem + (uint32_t)(b * 128);
+        if (offd) {
+          // one chunk per period: tile I in stage s0, tile J in stage s1
+          const int s0 = it % STAGES, s1 = (it + 1) % STAGES;
+          if (!tc::mbar_wait(full_bar(s0), (it / STAGES) & 1, abort_flag) ||
+              !tc::mbar_wait(full_bar(s1), ((it + 1) / STAGES) & 1, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t ih = sbase + (uint32_t)(s0 * STAGE_BYTES), il = ih + TILE;
+          const uint32_t jh = sbase + (uint32_t)(s1 * STAGE_BYTES), jl = jh + TILE;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const uint64_t djh = tc::desc_sw128(jh + 32u * k), djl = tc::desc_sw128(jl + 32u * k);
+            const uint64_t dih = tc::desc_sw128(ih + 32u * k), dil = tc::desc_sw128(il + 32u * k);
+            // D[j][i] (TMEM lane = row of block J)
+            tc::mma_tf32(d, djh, dih, IDESC, k == 0 ? 0u : 1u);
+            tc::mma_tf32(d, djh, dil, IDESC, 1u);
+            tc::mma_tf32(d, djl, dih, IDESC, 1u);
+          }
+          issued = true;
+          tc::mma_commit(empty_bar(s0));
+          tc::mma_commit(empty_bar(s1));
+          it += 2;
+          tc::mma_commit(accf_bar(b));
+          continue;
+        }
         const int end = std::min(nmine, it + PERIOD);
         for (bool first = true; it < end; ++it, first = false) {
           const int s = it % STAGES, n = it / STAGES;
@@ -321,7 +377,9 @@ __global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb)
 
   tc::fence_before_sync();
   __syncthreads();
-  // split partial, stored transposed (the reduction symmetrises)
+  // split partial of block (I, J), stored column-major: entry (i, j) of a
+  // diagonal block at [j][i] (the reduction symmetrises), entry (i, j) of an
+  // off-diagonal block (TMEM lane = j) at [i][j]
   const bool bad = *abort_flag != 0;
   double* out = a.split + (i64)blockIdx.x * (128 * 128);
   if (warp >= EPI0 && warp < MMA_WARP) {
@@ -340,7 +398,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb)
         const int col = c0 + j;
         double v = (double)__uint_as_float(sv[j]) + (double)__uint_as_float(cv[j]);
         if (nper == 0) v = 0.0;
-        if (col == row) v = diag[row];
+        if (!offd && col == row) v = diag[row];
         if (bad) v = __longlong_as_double(0x7ff8000000000000ll);
         out[(i64)col * 128 + row] = v;
       }
@@ -367,8 +425,9 @@ bool g_configured = false;
 }  // namespace
 
 bool gram_tc_eligible(const GramArgs<float>& a) {
-  return a.B == nullptr && !a.src_cur_pair && a.N >= 1 && a.N <= 128;
+  return a.B == nullptr && !a.src_cur_pair && a.N >= 1 && a.N <= MAXN;
 }
+
 
 void configure_gram_tc() {
   if (g_configured) return;
@@ -383,7 +442,9 @@ void launch_gram_tc(const GramArgs<float>& a, int nsplit, cudaStream_t s) {
   configure_gram_tc();
   const i64 nkb = (a.ng + KB - 1) / KB;
   prof_begin(gram_prof_name(a.trial, a.src_trial_slot, a.src_cur_pair), s);
-  // one split per CTA; a CTA without stages writes zeros
+  // one CTA per (split, block pair); a CTA without stages writes zeros
+  const int nsup = (a.N + 127) / 128;
+  const int nblk = nsplit * (nsup * (nsup + 1) / 2);
   // the source rows of the mode: W[cur] and HW[cur] (trial), W[1 - cur], or A
   bool vec = (a.ng % 4) == 0;
   auto aligned = [](const float* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
@@ -394,13 +455,13 @@ void launch_gram_tc(const GramArgs<float>& a, int nsplit, cudaStream_t s) {
   }
   if (a.trial) {
     if (vec)
-      k_gram_tc<true, true><<<nsplit, NTHR, SMEM_BYTES, s>>>(a, nkb);
+      k_gram_tc<true, true><<<nblk, NTHR, SMEM_BYTES, s>>>(a, nkb);
     else
-      k_gram_tc<false, true><<<nsplit, NTHR, SMEM_BYTES, s>>>(a, nkb);
+      k_gram_tc<false, true><<<nblk, NTHR, SMEM_BYTES, s>>>(a, nkb);
   } else if (vec) {
-    k_gram_tc<true, false><<<nsplit, NTHR, SMEM_BYTES, s>>>(a, nkb);
+    k_gram_tc<true, false><<<nblk, NTHR, SMEM_BYTES, s>>>(a, nkb);
   } else {
-    k_gram_tc<false, false><<<nsplit, NTHR, SMEM_BYTES, s>>>(a, nkb);
+    k_gram_tc<false, false><<<nblk, NTHR, SMEM_BYTES, s>>>(a, nkb);
   }
   prof_end(s);
 }

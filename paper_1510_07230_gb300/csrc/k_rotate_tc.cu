@@ -462,6 +462,405 @@ __global__ void __launch_bounds__(NTHR, 1) k_rotate_tc(RotArgs<float> a, i64 nti
   }
 }
 
+
+// ===========================================================================
+// N > 128 (up to 512 orbitals).  Output columns j are taken in chunks of 128
+// (passes jc = 0 .. nb - 1 over each tile); pass jc accumulates the K atoms
+// k = 0 .. 4 jc + 3 (orbitals i < 128 (jc + 1), the others have R_ij = 0).
+// R^-1 is too large for shared memory: it is split into TF32 pairs and laid
+// out in the swizzled operand format once per launch (k_rimg, one 32 KB
+// image per (jc, k)), and each atom's image is streamed into one of two R
+// slots with cp.async by the producers, one atom ahead.  X atoms cycle
+// through the four X slots; the last four atoms of a pass are the chunk's
+// own orbitals, whose X values the epilogue needs for the self term, so a
+// slot's first use in a pass also waits for the previous pass's epilogue to
+// release it.  The density of a point is summed over the passes of its tile.
+// Accumulators as above, with hh0 taking the first half of a pass's atoms.
+constexpr int BIG_MAXN = 512;
+constexpr int B_OFF_R = 0;                             // two R atom slots (hi rows, then lo rows)
+constexpr int B_OFF_X = 2 * SLOT;                      // four X atom slots
+constexpr int B_OFF_SELF = B_OFF_X + 4 * SLOT;         // BIG_MAXN x float2: R_jj (hi, lo)
+constexpr int B_OFF_COEF = B_OFF_SELF + BIG_MAXN * 8;  // BIG_MAXN x float2: 1 + tau sigma_i
+constexpr int B_OFF_DENS = B_OFF_COEF + BIG_MAXN * 8;
+constexpr int B_OFF_BAR = B_OFF_DENS + 4 * 32 * 8;
+// barriers: fullx[4], emptyx[4], xfree[4], fullr[2], emptyr[2], accf, acce, fin
+constexpr int B_NBAR = 19;
+constexpr int B_OFF_MISC = B_OFF_BAR + B_NBAR * 8;
+constexpr int B_SMEM = B_OFF_MISC + 16 + 1024;
+constexpr uint32_t IDESC128 = tc::idesc_tf32(128, 128);
+static_assert(B_SMEM <= 232448, "tensor-core rotation (N > 128) exceeds the shared-memory opt-in limit");
+
+__host__ __device__ constexpr int big_atoms(int jc) { return 4 * jc + 4; }
+__host__ __device__ constexpr int big_atom0(int jc) { return 2 * jc * (jc + 1); }  // image index of (jc, 0)
+
+// split R^-1 (strictly upper part) into the per-(jc, k) operand images
+__global__ void __launch_bounds__(256) k_rimg(RotArgs<float> a) {
+  if (a.st && a.st->done) return;
+  if (!gate_open(a.st, a.gate)) return;
+  const int N = a.N, nb = (N + 127) / 128;
+  int jc = 0;
+  while (jc + 1 < nb && big_atom0(jc + 1) <= (int)blockIdx.x) ++jc;
+  const int k = (int)blockIdx.x - big_atom0(jc);
+  unsigned char* base = reinterpret_cast<unsigned char*>(a.rimg) + (size_t)blockIdx.x * SLOT;
+  for (int idx = threadIdx.x; idx < 128 * 32; idx += 256) {
+    const int r = idx >> 5, il = idx & 31;
+    const int i = 32 * k + il, j = 128 * jc + r;
+    double v = 0.0;
+    if (i < j && j < N) v = a.Rinv[(i64)i * N + j];
+    const float hi = tc::to_tf32((float)v);
+    const float lo = tc::to_tf32((float)(v - (double)hi));
+    const int off = r * 128 + (((il >> 2) ^ (r & 7)) << 4) + (il & 3) * 4;
+    *reinterpret_cast<float*>(base + off) = hi;
+    *reinterpret_cast<float*>(base + ATOM + off) = lo;
+  }
+}
+
+__global__ void __launch_bounds__(NTHR, 1) k_rotate_tc_big(RotArgs<float> a, i64 ntiles) {
+  extern __shared__ unsigned char smem_raw[];
+  if (a.st && a.st->done) return;
+  if (!gate_open(a.st, a.gate)) return;
+
+  const uint32_t raw_addr = tc::smem_u32(smem_raw);
+  const uint32_t pad = (1024u - (raw_addr & 1023u)) & 1023u;
+  unsigned char* smem = smem_raw + pad;
+  const uint32_t sbase = raw_addr + pad;
+  float2* self = reinterpret_cast<float2*>(smem + B_OFF_SELF);
+  float2* coefs = reinterpret_cast<float2*>(smem + B_OFF_COEF);
+  float2* dens = reinterpret_cast<float2*>(smem + B_OFF_DENS);
+  const uint32_t bar0 = sbase + B_OFF_BAR;
+  auto fullx = [&](int k) { return bar0 + 8u * k; };
+  auto emptyx = [&](int k) { return bar0 + 8u * (4 + k); };
+  auto xfree = [&](int k) { return bar0 + 8u * (8 + k); };
+  auto fullr = [&](int k) { return bar0 + 8u * (12 + k); };
+  auto emptyr = [&](int k) { return bar0 + 8u * (14 + k); };
+  const uint32_t accf_bar = bar0 + 8u * 16, acce_bar = bar0 + 8u * 17, fin_bar = bar0 + 8u * 18;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + B_OFF_MISC);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + B_OFF_MISC + 4);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int N = a.N;
+  const i64 ng = a.ng;
+  const int nb = (N + 127) / 128, per_tile = big_atom0(nb);
+
+  int cur = 0;
+  const float* Wsrc;
+  const float* Hsrc = nullptr;
+  float* out;
+  double* rho;
+  double tau = 0.0;
+  if (a.trial) {
+    cur = a.st->cur;
+    Wsrc = a.W[cur];
+    Hsrc = a.HW[cur];
+    out = a.Wout[1 - cur];
+    rho = a.rho[1 - cur];
+    tau = a.st->tau_trial;
+  } else if (a.st) {
+    cur = a.st->cur;
+    Wsrc = a.src_trial_slot ? a.Wout[1 - cur] : a.A;
+    out = a.Wout[1 - cur];
+    rho = a.rho[1 - cur];
+  } else {
+    Wsrc = a.A;
+    out = a.B;
+    rho = a.rho_out;
+  }
+  const float tauH = (float)tau, tauL = (float)(tau - (double)tauH);
+  const unsigned char* img = reinterpret_cast<const unsigned char*>(a.rimg);
+
+  for (int j = tid; j < BIG_MAXN; j += NTHR) {
+    double A = 0.0, cf = 1.0;
+    if (j < N) {
+      A = a.Rinv[(i64)j * N + j];
+      if (a.trial) cf = 1.0 + tau * a.sigma[cur][j];
+    }
+    const float ah = (float)A, ch = (float)cf;
+    self[j] = make_float2(ah, (float)(A - (double)ah));
+    coefs[j] = make_float2(ch, (float)(cf - (double)ch));
+  }
+  if (tid == 0) {
+    for (int k = 0; k < 4; ++k) {
+      tc::mbar_init(fullx(k), PROD_WARPS * 32);
+      tc::mbar_init(emptyx(k), 1);
+      tc::mbar_init(xfree(k), 4);
+    }
+    for (int k = 0; k < 2; ++k) {
+      tc::mbar_init(fullr(k), PROD_WARPS * 32);
+      tc::mbar_init(emptyr(k), 1);
+    }
+    tc::mbar_init(accf_bar, 1);
+    tc::mbar_init(acce_bar, EPI_WARPS * 32);
+    tc::mbar_init(fin_bar, 1);
+    *abort_flag = 0;
+    tc::mbar_init_fence();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tc::smem_u32(tmem_slot), TMEM_COLS);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  const i64 G = gridDim.x;
+  const i64 t0 = ntiles * (i64)blockIdx.x / G, t1 = ntiles * (i64)(blockIdx.x + 1) / G;
+  const int nmine = (int)(t1 - t0);
+  const int ntot = nmine * per_tile;  // atoms of this CTA
+  const bool vec4 = (ng % 4 == 0) && ((reinterpret_cast<uintptr_t>(Wsrc) & 15u) == 0) &&
+                    (Hsrc == nullptr || (reinterpret_cast<uintptr_t>(Hsrc) & 15u) == 0);
+  // atom u -> (tile tt, pass jc, K atom k)
+  auto decode = [&](int u, int& tt, int& jc, int& k) {
+    tt = u / per_tile;
+    k = u - tt * per_tile;
+    jc = 0;
+    while (k >= big_atoms(jc)) {
+      k -= big_atoms(jc);
+      ++jc;
+    }
+  };
+
+  if (warp < PROD_WARPS) {
+    // ------------------------------------------------------------ producers
+    const int q = lane & 7, isub = lane >> 3;
+    auto issue = [&](int u, float4 (&wv)[4], float4 (&hv)[4]) {
+      int tt, jc, k;
+      decode(u, tt, jc, k);
+      const i64 p0 = (t0 + tt) * TPTS + 4 * q;
+      const int i = 32 * k + 4 * warp + isub;
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        wv[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+        hv[g] = wv[g];
+      }
+      if (i >= N) return;
+      const i64 base = (i64)i * ng + p0;
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        const i64 p = p0 + 32 * g;
+        if (vec4) {
+          if (p < ng) {
+            wv[g] = __ldg(reinterpret_cast<const float4*>(Wsrc + base + 32 * g));
+            if (Hsrc) hv[g] = __ldg(reinterpret_cast<const float4*>(Hsrc + base + 32 * g));
+          }
+        } else {
+          float w1[4] = {0.f, 0.f, 0.f, 0.f}, h1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (p + e < ng) {
+              w1[e] = Wsrc[base + 32 * g + e];
+              if (Hsrc) h1[e] = Hsrc[base + 32 * g + e];
+            }
+          wv[g] = make_float4(w1[0], w1[1], w1[2], w1[3]);
+          hv[g] = make_float4(h1[0], h1[1], h1[2], h1[3]);
+        }
+      }
+    };
+    // R image of atom u into R slot u & 1 (cp.async, completed one step later)
+    auto rcopy = [&](int u) {
+      int tt, jc, k;
+      decode(u, tt, jc, k);
+      const unsigned char* src = img + (size_t)(big_atom0(jc) + k) * SLOT;
+      const uint32_t dst = sbase + B_OFF_R + (uint32_t)((u & 1) * SLOT);
+      for (int c = tid; c < SLOT / 16; c += PROD_WARPS * 32) tc::cp_async16(dst + 16u * c, src + 16 * c);
+      tc::cp_async_commit();
+    };
+    bool issued = false;
+    auto step = [&](int u, const float4 (&w)[4], const float4 (&h)[4], float4 (&wl)[4], float4 (&hl)[4]) -> bool {
+      if (u + 2 < ntot) issue(u + 2, wl, hl);
+      int tt, jc, k;
+      decode(u, tt, jc, k);
+      const int P = tt * nb + jc, slot = u & 3;
+      // X slot: the MMAs of its previous atom are done, and for a pass's
+      // first use, the previous pass's epilogue has read its columns
+      if (u >= 4 && !tc::mbar_wait(emptyx(slot), ((u >> 2) - 1) & 1, abort_flag)) return false;
+      if (k < 4 && P > 0 && !tc::mbar_wait(xfree(slot), (P - 1) & 1, abort_flag)) return false;
+      unsigned char* xs = smem + B_OFF_X + slot * SLOT;
+      const float2 cf = coefs[min(32 * k + 4 * warp + isub, BIG_MAXN - 1)];
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        const float x[4] = {w[g].x, w[g].y, w[g].z, w[g].w};
+        const float h4[4] = {h[g].x, h[g].y, h[g].z, h[g].w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int row = 32 * g + 8 * e + q;
+          float hi, lo;
+          if (Hsrc) {
+            tc::trial_split(cf.x, cf.y, x[e], tauH, tauL, h4[e], hi, lo);
+          } else {
+            hi = tc::to_tf32(x[e]);
+            lo = x[e] - hi;
+          }
+          const int off = row * 128 + ((warp ^ q) << 4) + isub * 4;
+          *reinterpret_cast<float*>(xs + off) = hi;
+          *reinterpret_cast<float*>(xs + ATOM + off) = lo;
+        }
+      }
+      // this thread's R copies for atom u (issued one step earlier) have landed
+      tc::cp_async_wait_all();
+      tc::fence_proxy_async_smem();
+      tc::mbar_arrive(fullx(slot));
+      tc::mbar_arrive(fullr(u & 1));
+      if (warp == 0) {
+        // ---------------------------------------------------- MMA issue
+        int ok = 1;
+        if (lane == 0) {
+          const int natoms = big_atoms(jc), half = natoms / 2;
+          if (k == 0 && P > 0) ok = tc::mbar_wait(acce_bar, (P - 1) & 1, abort_flag);
+          if (ok) ok = tc::mbar_wait(fullx(slot), (u >> 2) & 1, abort_flag);
+          if (ok) ok = tc::mbar_wait(fullr(u & 1), (u >> 1) & 1, abort_flag);
+          if (ok) {
+            tc::fence_after_sync();
+            const uint32_t xh = sbase + B_OFF_X + slot * SLOT, xl = xh + ATOM;
+            const uint32_t rh = sbase + B_OFF_R + (u & 1) * SLOT, rl = rh + ATOM;
+            const uint32_t dhh = tmem + (k < half ? 0u : COL_HH1), dx = tmem + COL_X;
+#pragma unroll
+            for (int s4 = 0; s4 < 4; ++s4) {
+              const uint64_t axh = tc::desc_sw128(xh + 32u * s4), axl = tc::desc_sw128(xl + 32u * s4);
+              const uint64_t brh = tc::desc_sw128(rh + 32u * s4), brl = tc::desc_sw128(rl + 32u * s4);
+              tc::mma_tf32(dhh, axh, brh, IDESC128, ((k == 0 || k == half) && s4 == 0) ? 0u : 1u);
+              tc::mma_tf32(dx, axh, brl, IDESC128, (k == 0 && s4 == 0) ? 0u : 1u);
+              tc::mma_tf32(dx, axl, brh, IDESC128, 1u);
+            }
+            issued = true;
+            tc::mma_commit(emptyx(slot));
+            tc::mma_commit(emptyr(u & 1));
+            if (k == natoms - 1) tc::mma_commit(accf_bar);
+          }
+        }
+        if (!__shfl_sync(0xffffffffu, ok, 0)) return false;
+      }
+      // R image of atom u + 1 into the other slot once the MMAs of atom u - 1 are done with it
+      if (u + 1 < ntot) {
+        if (u + 1 >= 2 && !tc::mbar_wait(emptyr((u + 1) & 1), (((u + 1) >> 1) - 1) & 1, abort_flag)) return false;
+        rcopy(u + 1);
+      }
+      return true;
+    };
+    float4 wA[4], hA[4], wB[4], hB[4], wC[4], hC[4];
+    if (ntot > 0) {
+      issue(0, wA, hA);
+      rcopy(0);
+    }
+    if (ntot > 1) issue(1, wB, hB);
+    for (int u = 0; u < ntot; u += 3) {
+      if (!step(u, wA, hA, wC, hC)) break;
+      if (u + 1 >= ntot || !step(u + 1, wB, hB, wA, hA)) break;
+      if (u + 2 >= ntot || !step(u + 2, wC, hC, wB, hB)) break;
+    }
+    tc::cp_async_wait_all();
+    if (warp == 0 && lane == 0 && issued) {
+      tc::mma_commit(fin_bar);
+      tc::mbar_wait(fin_bar, 0, abort_flag, 4000000000ull);
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int quad = warp & 3;
+    const int jh = (warp - EPI0) >> 2;
+    const int pt = 32 * quad + 4 * (lane & 7) + (lane >> 3);
+    const int row = 32 * quad + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
+    const uint32_t off_col = COL_OFF + (uint32_t)(64 * jh);
+    const unsigned seed32 = mix32((unsigned)(a.st ? a.st->passes : 0) * 4u + (unsigned)a.sr_salt + 0x85ebca6bu);
+    float rs[4] = {0.f, 0.f, 0.f, 0.f}, rc[4] = {0.f, 0.f, 0.f, 0.f};
+    const int npass = nmine * nb;
+    for (int P = 0; P < npass; ++P) {
+      const int tt = P / nb, jc = P - tt * nb;
+      const i64 p = (t0 + tt) * TPTS + pt;
+      if (!tc::mbar_wait(accf_bar, P & 1, abort_flag)) break;
+      tc::fence_after_sync();
+#pragma unroll 1
+      for (int c = 0; c < 64; c += 16) {
+        uint32_t h0[16], h1[16], xx[16];
+        tc::tmem_ld16(lane_base + (uint32_t)(64 * jh + c), h0);
+        tc::tmem_ld16(lane_base + COL_HH1 + (uint32_t)(64 * jh + c), h1);
+        tc::tmem_ld16(lane_base + COL_X + (uint32_t)(64 * jh + c), xx);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int m = 0; m < 16; ++m)
+          h0[m] = __float_as_uint((__uint_as_float(h0[m]) + __uint_as_float(h1[m])) + __uint_as_float(xx[m]));
+        tc::tmem_st16(lane_base + off_col + (uint32_t)c, h0);
+      }
+      tc::tmem_wait_st();
+      tc::fence_before_sync();
+      tc::mbar_arrive(acce_bar);
+
+      if (jc == 0) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) rs[c] = rc[c] = 0.f;
+      }
+#pragma unroll 1
+      for (int g = 0; g < 8; ++g) {
+        uint32_t ov[8];
+        tc::tmem_ld8(lane_base + off_col + (uint32_t)(8 * g), ov);
+        const int jl0 = 64 * jh + 8 * g, j0 = 128 * jc + jl0;
+        const unsigned char* xs = smem + B_OFF_X + (jl0 >> 5) * SLOT;
+        float xh[8], xl[8];
+#pragma unroll
+        for (int h4 = 0; h4 < 2; ++h4) {
+          const int chunk = ((jl0 & 31) >> 2) + h4;
+          const int off = row * 128 + ((chunk ^ (row & 7)) << 4);
+          const float4 vh = *reinterpret_cast<const float4*>(xs + off);
+          const float4 vl = *reinterpret_cast<const float4*>(xs + ATOM + off);
+          xh[4 * h4 + 0] = vh.x, xh[4 * h4 + 1] = vh.y, xh[4 * h4 + 2] = vh.z, xh[4 * h4 + 3] = vh.w;
+          xl[4 * h4 + 0] = vl.x, xl[4 * h4 + 1] = vl.y, xl[4 * h4 + 2] = vl.z, xl[4 * h4 + 3] = vl.w;
+        }
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int m4 = 0; m4 < 8; m4 += 4) {
+          const unsigned bits = mix32(seed32 ^ mix32((unsigned)((j0 + m4) >> 2) * 0x9e3779b1u ^ (unsigned)p));
+#pragma unroll
+          for (int m = m4; m < m4 + 4; ++m) {
+            const int j = j0 + m;
+            const float2 c = self[min(j, BIG_MAXN - 1)];
+            const float d = dither(xh[m], (bits >> (8 * (m - m4))) & 0xffu);
+            const float o = fmaf(c.x, xh[m], fmaf(c.x, xl[m], fmaf(c.y, xh[m], __uint_as_float(ov[m]) + d)));
+            if (p < ng && j < N) {
+              out[(i64)j * ng + p] = o;
+              const float sq = o * o;
+              f2_add(rs[m - m4], rc[m - m4], sq, fmaf(o, o, -sq));
+            }
+          }
+        }
+        if ((g & 3) == 3) {
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(xfree(2 * jh + (g >> 2)));
+        }
+      }
+      if (jc == nb - 1 && rho != nullptr) {
+        float s0 = rs[0], c0 = rc[0], s2 = rs[2], c2 = rc[2];
+        f2_add(s0, c0, rs[1], rc[1]);
+        f2_add(s2, c2, rs[3], rc[3]);
+        f2_add(s0, c0, s2, c2);
+        float2* dq = dens + quad * 32;
+        if (jh == 1) dq[lane] = make_float2(s0, c0);
+        named_bar(1 + quad, 64);
+        if (jh == 0 && p < ng) {
+          const float2 o2 = dq[lane];
+          rho[p] = F_OCC * (((double)s0 + (double)c0) + ((double)o2.x + (double)o2.y));
+        }
+        named_bar(1 + quad, 64);
+      }
+    }
+  }
+
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, TMEM_COLS);
+  }
+  if (*abort_flag != 0 && tid == 0) {
+    atomicAdd(&g_rotate_tc_aborts, 1u);
+    if (a.st) {
+      State* w = const_cast<State*>(a.st);
+      w->status = 3;
+      w->done = 1;
+    }
+  }
+}
+
 bool g_configured = false;
 
 }  // namespace
@@ -474,14 +873,25 @@ int rotate_tc_grid(i64 ng) {
 void configure_rotate_tc() {
   if (g_configured) return;
   cudaFuncSetAttribute(k_rotate_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  cudaFuncSetAttribute(k_rotate_tc_big, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SMEM);
   g_configured = true;
+}
+
+size_t rotate_rimg_bytes(int N) {
+  if (N <= 128) return 0;
+  return (size_t)big_atom0((N + 127) / 128) * SLOT;
 }
 
 void launch_rotate_tc(const RotArgs<float>& a, cudaStream_t s) {
   configure_rotate_tc();
   const i64 ntiles = (a.ng + TPTS - 1) / TPTS;
   prof_begin(rotate_prof_name(a.trial, a.src_trial_slot, a.src_cur_slot), s);
-  k_rotate_tc<<<rotate_tc_grid(a.ng), NTHR, SMEM_BYTES, s>>>(a, ntiles);
+  if (a.N <= 128) {
+    k_rotate_tc<<<rotate_tc_grid(a.ng), NTHR, SMEM_BYTES, s>>>(a, ntiles);
+  } else {
+    k_rimg<<<big_atom0((a.N + 127) / 128), 256, 0, s>>>(a);
+    k_rotate_tc_big<<<rotate_tc_grid(a.ng), NTHR, B_SMEM, s>>>(a, ntiles);
+  }
   prof_end(s);
 }
 

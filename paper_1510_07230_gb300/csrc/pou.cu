@@ -117,6 +117,7 @@ struct pou_ctx {
   double* split;
   size_t split_elems;
   double* evec;      // eigenvector scratch of the subspace diagonalisation
+  float* rimg;       // split R^-1 image of the FP32 tensor-core rotation (N > 128)
   void* dv;          // V(trial) - V(current), working type (written by the potential pass)
   State* st;
   double* hist_E;
@@ -266,6 +267,7 @@ void enqueue_second_orth(pou_ctx* c) {
   launch_gram_reduce(r, s);
   launch_cholinv(c->st, c->S, c->Rinv, c->N, nullptr, c->st, pivot_tol(c), -1.0, s);
   RotArgs<T> ra{};
+  ra.rimg = c->rimg;
   ra.st = c->st;
   for (int k = 0; k < 2; ++k) {
     ra.Wout[k] = tp<T>(c->W[k]);
@@ -316,6 +318,7 @@ void enqueue_diag(pou_ctx* c) {
   launch_gram_reduce(r, s);
   launch_eigh(c->st, c->S, c->Rinv, c->evec, c->sigma[0], c->sigma[1], c->N, s);
   RotArgs<T> ra{};
+  ra.rimg = c->rimg;
   ra.st = c->st;
   for (int k = 0; k < 2; ++k) ra.Wout[k] = tp<T>(c->W[k]);
   ra.Rinv = c->Rinv;
@@ -411,6 +414,7 @@ void enqueue_pass(pou_ctx* c) {
   launch_cholinv(c->st, c->S, c->Rinv, c->N, nullptr, c->st, pivot_tol(c), reorth_thr(c), s);
   // W_new = Wt R^-1 and rho into the other pair
   RotArgs<T> ra{};
+  ra.rimg = c->rimg;
   ra.st = c->st;
   for (int k = 0; k < 2; ++k) {
     ra.W[k] = tp<T>(c->W[k]);
@@ -521,6 +525,7 @@ pou_status init_from_staged(pou_ctx* c) {
   launch_gram_reduce(r, s);
   launch_cholinv(c->st, c->S, c->Rinv, c->N, c->info, c->st, pivot_tol(c), reorth_thr(c), s);
   RotArgs<T> ra{};
+  ra.rimg = c->rimg;
   ra.st = c->st;
   for (int k = 0; k < 2; ++k) {
     ra.Wout[k] = tp<T>(c->W[k]);
@@ -845,6 +850,8 @@ pou_status pou_create(const pou_config* cfg, pou_ctx** out) {
   if (!(cfg->rho1 >= 0.0) || cfg->max_backtrack < 0 || cfg->max_backtrack > 60) return POU_EINVAL;
   if (!(cfg->tau_min > 0.0) || !(cfg->tau_max >= cfg->tau_min)) return POU_EINVAL;
   if (cfg->n_org != 1 || cfg->n_diag < 0) return POU_EINVAL;
+  // N > 128: FP32 form only, without the subspace diagonalisation
+  if (cfg->N > POU_MAX_N_FP64 && (cfg->precision != POU_FP32 || cfg->n_diag > 0)) return POU_EINVAL;
   const long long ng = (long long)cfg->n[0] * cfg->n[1] * cfg->n[2];
   if ((long long)cfg->N > ng) return POU_EINVAL;
 
@@ -912,17 +919,22 @@ static pou_status create_buffers(pou_ctx* c) {
     int nsplit, npair;
     i64 chunk;
     int ST;
-    // sized for the general product (Sigma of Algorithm M), which covers the symmetric Gram
-    if (c->dt == 0) {
-      gram_layout<double>(c->ng, c->N, true, &nsplit, &npair, &chunk);
-      ST = gram_supertile<double>();
-    } else {
-      gram_layout<float>(c->ng, c->N, true, &nsplit, &npair, &chunk);
-      ST = gram_supertile<float>();
+    // the larger of the symmetric Gram's and the general product's (Sigma) layouts
+    size_t elems = 0;
+    for (int general = 0; general < 2; ++general) {
+      if (c->dt == 0) {
+        gram_layout<double>(c->ng, c->N, general != 0, &nsplit, &npair, &chunk);
+        ST = gram_supertile<double>();
+      } else {
+        gram_layout<float>(c->ng, c->N, general != 0, &nsplit, &npair, &chunk);
+        ST = gram_supertile<float>();
+      }
+      elems = std::max(elems, (size_t)nsplit * npair * ST * ST);
     }
-    c->split_elems = (size_t)nsplit * npair * ST * ST;
+    c->split_elems = elems;
     DALLOC(c->split, c->split_elems * sizeof(double));
   }
+  if (c->dt == 1 && c->N > 128) DALLOC(c->rimg, rotate_rimg_bytes(c->N));
   DALLOC(c->evec, (size_t)c->N * c->N * sizeof(double));
   DALLOC(c->dv, c->ng * c->esz);
   DALLOC(c->st, sizeof(State));
@@ -943,7 +955,7 @@ void pou_destroy(pou_ctx* c) {
   void* ptrs[] = {c->W[0], c->W[1], c->HW[0], c->HW[1], c->V[0], c->V[1], c->rho[0], c->rho[1],
                   c->sigma[0], c->sigma[1], c->part[0], c->part[1], c->vext, c->work, c->tilepart,
                   c->epart, c->S, c->Rinv, c->split, c->evec, c->dv, c->st, c->hist_E, c->hist_tau, c->info,
-                  c->dR, c->dZ, c->tabs.gx, c->fpart, c->ublock, c->gblock, c->rho_e, c->V64_e};
+                  c->dR, c->dZ, c->tabs.gx, c->fpart, c->ublock, c->gblock, c->rho_e, c->V64_e, c->rimg};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->dt == 1) {
@@ -1202,6 +1214,7 @@ pou_status pou_gradient_norm(pou_ctx* c, double* out) {
   ProfScope prof_scope(c);
   if (!c || !out) return fail(c, POU_EINVAL, "bad argument");
   if (!c->have_orbitals) return fail(c, POU_EINVAL, "no orbitals set");
+  if (c->N > POU_MAX_N_FP64) return fail(c, POU_EINVAL, "gradient norm: N > %d not built", POU_MAX_N_FP64);
   int cur;
   pou_status e = cur_index(c, &cur);
   if (e != POU_OK) return e;
@@ -1495,6 +1508,7 @@ pou_status pou_rotate(int dtype, long long Ng, int N, const void* A, const doubl
   configure_kernels();
   if ((dtype != POU_DT_F64 && dtype != POU_DT_F32) || Ng < 1 || N < 1 || N > POU_MAX_N || !A || !Rinv || !B)
     return POU_EINVAL;
+  if (dtype == POU_DT_F64 && N > POU_MAX_N_FP64) return POU_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (dtype == POU_DT_F64) {
     RotArgs<double> ra{};
@@ -1513,7 +1527,13 @@ pou_status pou_rotate(int dtype, long long Ng, int N, const void* A, const doubl
     ra.Rinv = Rinv;
     ra.ng = Ng;
     ra.N = N;
+    // N > 128: stream-ordered scratch for the split R^-1 image, freed after the launch
+    if (N > 128 && cudaMallocAsync(reinterpret_cast<void**>(&ra.rimg), rotate_rimg_bytes(N), s) != cudaSuccess) {
+      cudaGetLastError();
+      return POU_ENOMEM;
+    }
     launch_rotate<float>(ra, s);
+    if (ra.rimg) cudaFreeAsync(ra.rimg, s);
   }
   return cudaGetLastError() == cudaSuccess ? POU_OK : POU_ECUDA;
 }

@@ -154,8 +154,11 @@ struct RotArgs {
   i64 ng;
   int N;
   int general;          // 1: full matrix (no triangular skip)
+  float* rimg;          // FP32 tensor-core rotation with N > 128: scratch of rotate_rimg_bytes(N)
 };
 int rotate_grid(i64 ng, int elem_bytes);
+// bytes of the split R^-1 image the FP32 tensor-core rotation needs for N > 128
+size_t rotate_rimg_bytes(int N);
 // FP32 rotation on the tensor cores (TF32 split products for the
 // off-diagonal part), N <= 128; one CTA per SM.
 int rotate_tc_grid(i64 ng);

@@ -92,17 +92,26 @@ def atoms(seed: int, n_atoms: int, L: float, z_recipe: str,
     return R, Z
 
 
-def random_orbitals(seed: int, N: int, n: Tuple[int, int, int], count: Optional[int] = None) -> np.ndarray:
-    """Raw initial orbitals, i.i.d. N(0,1), shape (N, nz, ny, nx), float64.
+def random_orbitals(seed: int, N: int, n: Tuple[int, int, int], count: Optional[int] = None,
+                    dtype=np.float64) -> np.ndarray:
+    """Raw initial orbitals, i.i.d. N(0,1), shape (N, nz, ny, nx).
 
     They are not orthonormal: each solver orthonormalises them itself.
     ``count`` < N returns only the first ``count`` orbitals of the same draw
     (the generator fills the array in order, so they are identical).
+    ``dtype=np.float32`` draws in single precision, orbital by orbital (a
+    different draw from the float64 one, and half the host memory: for the
+    largest workloads, whose float64 block would not be needed anyway).
     """
     nx, ny, nz = n
     rng = np.random.Generator(np.random.PCG64(seed + 1000003))
     k = N if count is None else min(int(count), N)
-    return rng.standard_normal((k, nz, ny, nx))
+    if dtype == np.float64:
+        return rng.standard_normal((k, nz, ny, nx))
+    out = np.empty((k, nz, ny, nx), dtype=np.float32)
+    for i in range(k):
+        out[i] = rng.standard_normal((nz, ny, nx), dtype=np.float32)
+    return out
 
 
 def random_field(seed: int, n: Tuple[int, int, int], lo: float = 0.0,
@@ -113,9 +122,12 @@ def random_field(seed: int, n: Tuple[int, int, int], lo: float = 0.0,
     return rng.uniform(lo, hi, size=(nz, ny, nx))
 
 
-def workload_inputs(name: str):
-    """(workload, R, Z, U0_raw) for one named workload."""
+def workload_inputs(name: str, dtype=None):
+    """(workload, R, Z, U0_raw) for one named workload; U0 in float64, or in
+    float32 for the workloads whose block exceeds 4 GB (unless ``dtype`` says)."""
     w = WORKLOADS[name]
     R, Z = atoms(w.seed, w.n_atoms, w.L, w.z_recipe)
-    U0 = random_orbitals(w.seed, w.N, (w.n, w.n, w.n))
+    if dtype is None:
+        dtype = np.float32 if w.N * w.n ** 3 * 8 > (4 << 30) else np.float64
+    U0 = random_orbitals(w.seed, w.N, (w.n, w.n, w.n), dtype=dtype)
     return w, R, Z, U0

@@ -157,6 +157,139 @@ def test_rotate_op_off_diagonal_sum_is_unbiased(P, N, ng):
     np.testing.assert_allclose(rho.cpu().numpy(), 2.0 * np.sum(ref * ref, 0), rtol=1e-6)
 
 
+# ------------------------------------------------------------------ N > 128 (FP32 form)
+@pytest.mark.parametrize("N,ng", [(129, 4099), (256, 20000), (300, 6001), (512, 9000)])
+def test_gram_op_block_pairs(P, N, ng):
+    """Tensor-core Gram over 128 x 128 block pairs: ragged last block, odd Ng."""
+    rng = np.random.default_rng(N * 11 + ng)
+    A = rng.standard_normal((N, ng))
+    Ad = dev(A, torch.float32)
+    ws = torch.empty(P.gram_workspace_bytes(P.DT_F32, ng, N) // 8 + 1, dtype=torch.float64, device="cuda")
+    S = torch.empty((N, N), dtype=torch.float64, device="cuda")
+    dV = 0.21
+    P.gram(Ad, dV, S, ws)
+    Ar = Ad.double().cpu().numpy()
+    ref = dV * Ar @ Ar.T
+    scale = dV * np.sqrt(np.outer(np.sum(Ar * Ar, 1), np.sum(Ar * Ar, 1)))
+    Sg = S.cpu().numpy()
+    assert np.max(np.abs(Sg - ref) / scale) < 2e-6
+    assert np.array_equal(Sg, Sg.T)
+
+
+def test_gram_op_block_pairs_coherent_sums(P):
+    N, ng = 384, 40000
+    rng = np.random.default_rng(17)
+    A = 1.0 + 0.3 * rng.standard_normal((N, ng)) + 0.2 * rng.random((N, 1))
+    Ad = dev(A, torch.float32)
+    ws = torch.empty(P.gram_workspace_bytes(P.DT_F32, ng, N) // 8 + 1, dtype=torch.float64, device="cuda")
+    S = torch.empty((N, N), dtype=torch.float64, device="cuda")
+    P.gram(Ad, 1.0 / ng, S, ws)
+    Ar = Ad.double().cpu().numpy()
+    ref = (Ar @ Ar.T) / ng
+    err = (S.cpu().numpy() - ref) / np.abs(ref)
+    assert np.max(np.abs(err)) < 1e-6, np.max(np.abs(err))
+    # the tensor core truncates at each of the 12-16 accumulations of a
+    # promotion period (64 points): a mean error of about -3e-7 of these
+    # coherent sums, the same on diagonal and off-diagonal blocks
+    assert abs(np.mean(err)) < 5e-7, np.mean(err)
+
+
+@pytest.mark.parametrize("N", [129, 200, 512])
+def test_cholinv_op_large(P, N):
+    rng = np.random.default_rng(N)
+    B = rng.standard_normal((N, N)) * 0.05
+    S = np.eye(N) + B @ B.T
+    Rinv = torch.empty((N, N), dtype=torch.float64, device="cuda")
+    info = torch.full((1,), 7, dtype=torch.int32, device="cuda")
+    P.cholinv(dev(S), Rinv, info)
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    import scipy.linalg as sl
+    R = sl.cholesky(S, lower=False)
+    np.testing.assert_allclose(Rinv.cpu().numpy(), np.linalg.inv(R), atol=1e-12 * np.linalg.cond(R))
+    np.testing.assert_allclose(np.tril(Rinv.cpu().numpy(), -1), 0.0)
+
+
+def test_cholinv_op_large_reports_non_spd(P):
+    N = 300
+    S = np.eye(N)
+    S[250, 250] = -1.0
+    Rinv = torch.empty((N, N), dtype=torch.float64, device="cuda")
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    P.cholinv(dev(S), Rinv, info)
+    torch.cuda.synchronize()
+    assert int(info.item()) == 251
+
+
+@pytest.mark.parametrize("N,ng", [(129, 4099), (256, 6000), (300, 2561), (512, 4096)])
+def test_rotate_op_large(P, N, ng):
+    """Chunked tensor-core rotation: output chunks of 128, R^-1 streamed per atom."""
+    rng = np.random.default_rng(N * 3 + ng)
+    A = rng.standard_normal((N, ng))
+    Bm = rng.standard_normal((N, N)) * 0.03
+    R = np.linalg.cholesky(np.eye(N) + Bm @ Bm.T).T
+    Rinv = np.linalg.inv(R)
+    Ad = dev(A, torch.float32)
+    Bd = torch.empty_like(Ad)
+    rho = torch.empty(ng, dtype=torch.float64, device="cuda")
+    P.rotate(Ad, dev(Rinv), Bd, rho)
+    Ar = Ad.double().cpu().numpy()
+    ref = Rinv.T @ Ar
+    np.testing.assert_allclose(Bd.double().cpu().numpy(), ref, atol=3e-6 * np.max(np.abs(ref)))
+    np.testing.assert_allclose(rho.cpu().numpy(), 2.0 * np.sum(ref * ref, 0), rtol=3e-5, atol=3e-6)
+
+
+def test_rotate_op_fp64_large_n_is_einval(P):
+    N, ng = 200, 1000
+    A = torch.zeros((N, ng), dtype=torch.float64, device="cuda")
+    with pytest.raises(P.PouError):
+        P.rotate(A, torch.eye(N, dtype=torch.float64, device="cuda"), torch.empty_like(A))
+
+
+def _large_n_system(N):
+    n, L = (16, 16, 18), (6.0, 6.0, 7.0)
+    R, Z, _ = _system(n, L, 1, 23, M=3)
+    U = inputs.random_orbitals(29, N, n)
+    return n, L, R, Z, U
+
+
+def test_iteration_large_n_fp32(P):
+    """N = 192 (two 128-row blocks, the chunked rotation and the multi-kernel
+    Cholesky inside the iteration): the first steps follow the FP64 oracle's
+    trajectory, and the energy and density the library reports are those of
+    the FP32 orbitals it returns, which stay orthonormal."""
+    N = 192
+    n, L, R, Z, U = _large_n_system(N)
+    cfg = ocfg(n, L, N)
+    vext = O.vext_gaussians(cfg, R, Z, 0.8)
+    s = solver(P, n, L, N, precision=1)
+    s.set_atoms(R, Z, 0.8)
+    s.set_orbitals(U.astype(np.float32))
+    s.iterate(6)
+    Eg, _ = s.history()
+    st = O.run(U.astype(np.float32).astype(np.float64), vext, cfg, 6)
+    Eo = np.array([h.energy for h in st.history])
+    np.testing.assert_allclose(Eg[:len(Eo)], Eo[:len(Eg)], rtol=2e-6)
+    s.iterate(40)
+    W = s.get_orbitals()
+    assert np.max(np.abs(O.inner_matrix(W, W, cfg) - np.eye(N))) < 2e-6
+    e = s.energy()["total"]
+    assert abs(O.energy(W, vext, cfg) - e) < 1e-7 * abs(e)
+    np.testing.assert_allclose(s.get_density(), O.density(W), rtol=1e-6, atol=1e-9)
+    E, _ = s.history()
+    assert np.all(np.isfinite(E)) and E[-1] < E[5]
+    with pytest.raises(P.PouError):
+        s.gradient_norm()  # not built for N > 128
+    s.close()
+
+
+def test_large_n_fp64_form_is_einval(P):
+    with pytest.raises(P.PouError):
+        solver(P, (16, 16, 18), (6.0, 6.0, 7.0), 192, precision=0)
+    with pytest.raises(P.PouError):
+        solver(P, (16, 16, 18), (6.0, 6.0, 7.0), 192, precision=1, n_diag=50)
+
+
 # ------------------------------------------------------------------ a6: Hartree
 @pytest.mark.parametrize("n,L", [((20, 12, 15), (7.0, 5.0, 6.0)), ((32, 32, 32), (10.0,) * 3),
                                  ((16, 10, 9), (4.0, 3.0, 3.3)), ((96, 6, 5), (20.0, 2.0, 2.0))])

@@ -42,8 +42,9 @@ def test_gram_noalloc_matches_gram_twice(dt, N, ng):
 
 def test_gram_noalloc_rejects_too_many_orbitals():
     from paper_1510_07230_gb300 import pou
-    A = torch.zeros((129, 64), dtype=torch.float32, device="cuda")
-    S = torch.zeros((129, 129), dtype=torch.float64, device="cuda")
+    N = pou.MAX_N + 1
+    A = torch.zeros((N, 64), dtype=torch.float32, device="cuda")
+    S = torch.zeros((N, N), dtype=torch.float64, device="cuda")
     with pytest.raises(pou.PouError) as ei:
         pou.gram_noalloc(A, 1.0, S)
     assert ei.value.status == pou.EINVAL
