@@ -237,7 +237,9 @@ def run_ours(args):
     w = inputs.WORKLOADS[args.workload]
     R, Z = inputs.atoms(w.seed, w.n_atoms, w.L, w.z_recipe)
     t0 = time.time()
-    U0 = inputs.random_orbitals(w.seed, w.N, (w.n, w.n, w.n))
+    # float32 draw for blocks above 4 GB in float64 (the 512-orbital workload)
+    big = w.N * w.n ** 3 * 8 > (4 << 30)
+    U0 = inputs.random_orbitals(w.seed, w.N, (w.n, w.n, w.n), dtype=np.float32 if big else np.float64)
     gen_s = time.time() - t0
     prec = pou.FP32 if args.precision == "fp32" else pou.FP64
     stream = torch.cuda.Stream()
@@ -308,10 +310,13 @@ def run_ours(args):
         if k in gated:
             kernels[k]["taken"] = eff
         if k in ("gram", "gram_reorth", "gram_plain") and prec == pou.FP32 and eff:
-            # tensor-core rate of the TF32 split products actually issued (two
-            # M=N=128, K=8 MMAs per 8 grid points: 4 * 128^2 * ng flops) and the
-            # Gram's own algorithmic flops (upper triangle)
-            kernels[k]["tensor_tflops_issued"] = round(4 * 128 * 128 * ng / (t_ / eff / 1e3) / 1e12, 1)
+            # tensor-core rate of the TF32 split products actually issued (per
+            # 8 grid points, M=N=128, K=8 MMAs: two on each diagonal 128-block,
+            # three on each off-diagonal one) and the Gram's own algorithmic
+            # flops (upper triangle)
+            nsup = (w.N + 127) // 128
+            mmas = 2 * nsup + 3 * nsup * (nsup - 1) // 2
+            kernels[k]["tensor_tflops_issued"] = round(mmas * 2 * 128 * 128 * ng / (t_ / eff / 1e3) / 1e12, 1)
             kernels[k]["gram_tflops"] = round(gram_flops(w.N, ng) / (t_ / eff / 1e3) / 1e12, 2)
     iter_kernels = [k for k in prof if k not in ("density", "forces", "potential_local", "convert", "scale_copy")]
     out = {
@@ -331,7 +336,7 @@ def run_ours(args):
     out["_iter_kernels"] = iter_kernels
 
     # FP64 form beside it (same workload, same U0)
-    if prec == pou.FP32 and args.fp64_steps > 0:
+    if prec == pou.FP32 and args.fp64_steps > 0 and w.N <= pou.MAX_N_FP64:
         s64 = make_solver(pou, w, pou.FP64, stream.cuda_stream, args.bb_variant)
         s64.set_atoms(R, Z, w.width)
         s64.set_orbitals(U0)

@@ -290,6 +290,42 @@ def test_large_n_fp64_form_is_einval(P):
         solver(P, (16, 16, 18), (6.0, 6.0, 7.0), 192, precision=1, n_diag=50)
 
 
+def test_full_size_512_orbitals(P):
+    """The 192^3 grid with N = 512 (14.5 GB per FP32 block), in the launch
+    configuration the bench times: properties that hold at any size, checked
+    with plain PyTorch FP64 on the returned orbitals (the oracle cannot run
+    at this size): orthonormality of the whole block, the density at sampled
+    points, and an energy that goes down."""
+    w, R, Z, U0 = inputs.workload_inputs("l40_g192_n512")
+    s = solver(P, w.n, w.L, w.N, order=w.order, precision=1, bb_variant=3)
+    s.set_atoms(R, Z, w.width)
+    s.set_orbitals(U0)
+    del U0
+    E0 = s.energy()["total"]
+    rep = s.iterate(4)
+    assert rep["status"] == P.OK and rep["iterations"] == 4
+    E, _ = s.history()
+    assert np.all(np.isfinite(E)) and E[-1] < E0
+    ng = w.n ** 3
+    dV = (w.L / w.n) ** 3
+    W = torch.empty((w.N, ng), dtype=torch.float32, device="cuda")
+    s.get_orbitals(W)
+    G = torch.zeros((w.N, w.N), dtype=torch.float64, device="cuda")
+    for a in range(0, ng, 1 << 20):
+        Wc = W[:, a:a + (1 << 20)].double()
+        G += Wc @ Wc.T
+        del Wc
+    G *= dV
+    ortho = (G - torch.eye(w.N, dtype=torch.float64, device="cuda")).abs().max().item()
+    assert ortho < 2e-6, ortho
+    rho = s.get_density()
+    idx = np.random.default_rng(3).choice(ng, 4096, replace=False)
+    Ws = W[:, torch.as_tensor(idx, device="cuda")].double()
+    ref = (2.0 * (Ws * Ws).sum(0)).cpu().numpy()
+    np.testing.assert_allclose(rho.reshape(-1)[idx], ref, rtol=1e-6)
+    s.close()
+
+
 # ------------------------------------------------------------------ a6: Hartree
 @pytest.mark.parametrize("n,L", [((20, 12, 15), (7.0, 5.0, 6.0)), ((32, 32, 32), (10.0,) * 3),
                                  ((16, 10, 9), (4.0, 3.0, 3.3)), ((96, 6, 5), (20.0, 2.0, 2.0))])
