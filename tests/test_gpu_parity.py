@@ -482,11 +482,10 @@ def test_converged_energy_matches_oracle_l10_g32_n4(P, precision, tol):
     e = s.energy()["total"]
     assert abs(e - Estar) <= tol, (e, Estar)
     # never below the minimum by more than the tolerance (normalisation errors
-    # would show here).  The mixed form has single-step transients: at a large
-    # Barzilai-Borwein step (tau ~ 10-40) the FP32 trial point is orthonormal to
-    # about 1e-7, and its energy can fall up to ~1.3e-6 Ha below E* for one step
-    # (measured over perturbed starts with both the tensor-core and the CUDA-core
-    # rotation); a systematic normalisation error would persist instead.
+    # would show here).  The bound for single steps of the mixed form leaves
+    # room for transients at large Barzilai-Borwein steps (tau ~ 10-45), where
+    # the trial block is furthest from orthonormal; the last 500 steps must
+    # stay within the target, where a systematic normalisation error would show.
     assert np.min(E) >= Estar - (tol if precision == 0 else 2e-6)
     if precision == 1:
         assert np.min(E[-500:]) >= Estar - tol  # no persistent dip near convergence
