@@ -2,7 +2,7 @@
 
 Tolerances.  FP64 form: the kernels reorder FP64 sums, so results agree to a
 few ulps times the condition of each quantity; energies to 1e-8 Ha over a
-200-step trajectory (the benchmark spec's bound).  FP32 form: inputs are rounded to
+200-step trajectory (the target bound).  FP32 form: inputs are rounded to
 FP32 first and the oracle runs on the rounded values, so the remaining error
 is FP32 arithmetic (2^-24 relative per operation, random sign, summed in FP64
 at the block level): 1e-5 relative for pointwise fields, 1e-6 Ha for energies.
