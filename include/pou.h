@@ -17,7 +17,8 @@
  * neutralising background) and Slater LDA exchange.  The solver returns the
  * energy, the orbitals and the density.
  *
- * Each iteration (Algorithm E, i.e. Algorithm M with n_org = 1; Sec. 3.2):
+ * Each iteration (Algorithm E, i.e. Algorithm M with n_org = 1; Sec. 3.2;
+ * Algorithm M's n_org > 1 and subspace diagonalisation are options below):
  * HW = H(rho) W, sigma_ii = <H w_i, w_i>, direction z_i = H w_i - sigma_ii w_i,
  * a shared Barzilai-Borwein step, nonmonotone backtracking (Eq. ene-de) and
  * Orth by Cholesky-QR (S = <Wt^T Wt>, S = R^T R, W = Wt R^-1), then the new
@@ -88,7 +89,10 @@ typedef struct {
   double tau0;        /* first step; <= 0 selects 1 / lambda_max(-1/2 Lap_h) */
   double tau_min;     /* step clamp: 1e-12 */
   double tau_max;     /* step clamp: 1e3 */
-  int n_org;          /* Algorithm M: Orth every n_org steps (only 1 is accepted) */
+  int n_org;          /* Algorithm M: Orth every n_org steps (>= 1; 1 = Algorithm E).  The
+                         steps in between take W - tau Z as it is (no Orth, no Eq. ene-de test,
+                         no backtracking); their history entries are NaN and pou_energy
+                         reports the last orthonormalised step's energy until the next one */
   int n_diag;         /* Algorithm M: subspace diagonalisation every n_diag steps
                          (Sec. 3.3: Sigma = <W^T H W>, P^T Sigma P diagonal, W <- W P);
                          0 = off */

@@ -28,7 +28,7 @@ constexpr int MAXB = 4;      // panels for N <= 128
 
 __global__ void __launch_bounds__(CNT) k_cholinv(const State* st_ro, State* st, const double* S,
                                                   double* Rinv, int N, int* info, double piv_rel,
-                                                  double reorth_thr) {
+                                                  double reorth_thr, int orth_gated) {
   extern __shared__ double A[];  // [N][N+1]: upper = R, strictly lower = X^T
   __shared__ double rdiag[128];  // 1 / R_ii
   __shared__ double T[MAXB - 1][NB][NB + 1];  // sums of one level of the inverse
@@ -37,6 +37,16 @@ __global__ void __launch_bounds__(CNT) k_cholinv(const State* st_ro, State* st, 
   __shared__ double dmax;
   if (st_ro && st_ro->done) return;
   if (reorth_thr < 0.0 && !(st_ro && st_ro->reorth)) return;  // gated second pass
+  if (orth_gated && st_ro && !st_ro->orth_now) {
+    // Algorithm M, intermediate step: no orthonormalisation, R^-1 = I
+    for (int idx = threadIdx.x; idx < N * N; idx += CNT) Rinv[idx] = (idx / N == idx % N) ? 1.0 : 0.0;
+    if (threadIdx.x == 0 && st) {
+      st->reorth = 0;
+      st->gram_off_trial = 0.0;
+      st->chol_info = 0;
+    }
+    return;
+  }
   const int ld = N + 1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   double om = 0.0;
@@ -238,10 +248,16 @@ struct BigArgs {
   int N;
   int* flag;        // 0, or 1 + the failing pivot
   double piv_rel, reorth_thr;
+  int orth_gated;   // trial pass: skipped (R^-1 = I) on the intermediate steps of Algorithm M
 };
+
+__device__ __forceinline__ bool big_intermediate(const BigArgs& a) {
+  return a.orth_gated && a.st && !a.st->orth_now;
+}
 
 __device__ __forceinline__ bool big_gated(const BigArgs& a) {
   if (a.st && a.st->done) return true;
+  if (big_intermediate(a)) return true;
   return a.reorth_thr < 0.0 && !(a.st && a.st->reorth);
 }
 
@@ -250,8 +266,19 @@ constexpr int BT = 32;  // panel / tile width
 // copy S into the working matrix; trial diagnostics as in the small kernel
 __global__ void __launch_bounds__(1024) k_big_init(BigArgs a) {
   __shared__ double offmax[32];
-  if (big_gated(a)) return;
   const int N = a.N, tid = threadIdx.x;
+  if (a.st && a.st->done) return;
+  if (big_intermediate(a)) {
+    // Algorithm M, intermediate step: no orthonormalisation, R^-1 = I
+    for (i64 idx = tid; idx < (i64)N * N; idx += 1024) a.A[idx] = (idx / N == idx % N) ? 1.0 : 0.0;
+    if (tid == 0 && a.st_rw) {
+      a.st_rw->reorth = 0;
+      a.st_rw->gram_off_trial = 0.0;
+      a.st_rw->chol_info = 0;
+    }
+    return;
+  }
+  if (big_gated(a)) return;
   double om = 0.0;
   for (i64 idx = tid; idx < (i64)N * N; idx += 1024) {
     const int i = (int)(idx / N), j = (int)(idx % N);
@@ -472,8 +499,8 @@ __global__ void __launch_bounds__(256) k_big_final(BigArgs a, int* info) {
 }
 
 void launch_cholinv_big(const State* st, const double* S, double* Rinv, int N, int* info, State* st_rw,
-                        double piv_rel, double reorth_thr, cudaStream_t s) {
-  BigArgs a{st, st_rw, S, Rinv, N, info ? info : &st_rw->chol_info, piv_rel, reorth_thr};
+                        double piv_rel, double reorth_thr, cudaStream_t s, bool orth_gated) {
+  BigArgs a{st, st_rw, S, Rinv, N, info ? info : &st_rw->chol_info, piv_rel, reorth_thr, orth_gated ? 1 : 0};
   const int np = (N + BT - 1) / BT;
   k_big_init<<<1, 1024, 0, s>>>(a);
   for (int p = 0; p < np; ++p) {
@@ -498,12 +525,13 @@ void configure_cholinv() {
 }
 
 void launch_cholinv(const State* st, const double* S, double* Rinv, int N, int* info, State* st_rw,
-                    double piv_rel, double reorth_thr, cudaStream_t s) {
+                    double piv_rel, double reorth_thr, cudaStream_t s, bool orth_gated) {
   prof_begin("cholinv", s);
   if (N <= 128) {  // one CTA is faster here than the multi-kernel path (0.34 vs 0.38 ms)
-    k_cholinv<<<1, CNT, cholinv_smem_bytes(N), s>>>(st, st_rw, S, Rinv, N, info, piv_rel, reorth_thr);
+    k_cholinv<<<1, CNT, cholinv_smem_bytes(N), s>>>(st, st_rw, S, Rinv, N, info, piv_rel, reorth_thr,
+                                                     orth_gated ? 1 : 0);
   } else {
-    launch_cholinv_big(st, S, Rinv, N, info, st_rw, piv_rel, reorth_thr, s);
+    launch_cholinv_big(st, S, Rinv, N, info, st_rw, piv_rel, reorth_thr, s, orth_gated);
   }
   prof_end(s);
 }

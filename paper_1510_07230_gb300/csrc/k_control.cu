@@ -135,11 +135,16 @@ __global__ void __launch_bounds__(KNT) k_control(CtrlArgs a) {
     st->reorth_count = 0;
     st->diag_now = 0;
     st->diag_count = 0;
+    st->orth_now = 1;
     st->done = 1;
     return;
   }
   st->passes += 1;
-  bool accept = E <= st->C - a.rho1 * st->tau_trial * st->znorm2;
+  // Algorithm M, intermediate step (n_org > 1): the trial W - tau Z is taken
+  // as it is, without Orth, the Eq. (ene-de) test or backtracking; C, Q and
+  // the reference energy stay those of the last orthonormalised step
+  const bool orth = st->orth_now != 0;
+  bool accept = !orth || E <= st->C - a.rho1 * st->tau_trial * st->znorm2;
   if (!accept && st->s >= a.max_backtrack) {
     accept = true;
     st->forced += 1;
@@ -150,22 +155,24 @@ __global__ void __launch_bounds__(KNT) k_control(CtrlArgs a) {
     st->tau_trial = st->tau_bb * pow(a.delta, (double)st->s);
     return;
   }
-  const double Qn = a.eta * st->Q + 1.0;
-  st->C = (a.eta * st->Q * st->C + E) / Qn;
-  st->Q = Qn;
-  const double df = fabs(st->E_cur - E) / (fabs(st->E_cur) + 1.0);
-  st->df[2] = st->df[1];
-  st->df[1] = st->df[0];
-  st->df[0] = df;
-  st->n_df += 1;
-  st->last_tau = st->tau_trial;
+  if (orth) {
+    const double Qn = a.eta * st->Q + 1.0;
+    st->C = (a.eta * st->Q * st->C + E) / Qn;
+    st->Q = Qn;
+    const double df = fabs(st->E_cur - E) / (fabs(st->E_cur) + 1.0);
+    st->df[2] = st->df[1];
+    st->df[1] = st->df[0];
+    st->df[0] = df;
+    st->n_df += 1;
+    st->last_tau = st->tau_trial;
+    st->E_cur = E;
+    for (int k = 0; k < 4; ++k) st->terms_cur[k] = st->terms_trial[k];
+    st->gram_off_acc = st->gram_off_trial;
+  }
   if (st->l < HIST_MAX) {
-    a.hist_E[st->l] = E;
+    a.hist_E[st->l] = orth ? E : NAN;  // no energy of a non-orthonormal iterate
     a.hist_tau[st->l] = st->tau_trial;
   }
-  st->E_cur = E;
-  for (int k = 0; k < 4; ++k) st->terms_cur[k] = st->terms_trial[k];
-  st->gram_off_acc = st->gram_off_trial;
   st->cur = t;
   st->l += 1;
   st->znorm2 = zz;
@@ -178,10 +185,12 @@ __global__ void __launch_bounds__(KNT) k_control(CtrlArgs a) {
   st->tau_bb = tau;
   st->tau_trial = tau;
   st->s = 0;
-  // Algorithm M: subspace diagonalisation every n_diag steps, before the next trial
-  st->diag_now = (a.n_diag > 0 && st->l % a.n_diag == 0) ? 1 : 0;
+  // Algorithm M: subspace diagonalisation every n_diag steps (after an
+  // orthonormalised step), before the next trial; Orth every n_org steps
+  st->diag_now = (orth && a.n_diag > 0 && st->l % a.n_diag == 0) ? 1 : 0;
+  st->orth_now = (a.n_org <= 1 || st->l % a.n_org == 0) ? 1 : 0;
   if (st->l >= st->target_l) st->done = 1;
-  if (st->e_tol > 0.0 && st->n_df >= 3 && (st->df[0] + st->df[1] + st->df[2]) / 3.0 < st->e_tol) {
+  if (orth && st->e_tol > 0.0 && st->n_df >= 3 && (st->df[0] + st->df[1] + st->df[2]) / 3.0 < st->e_tol) {
     st->converged = 1;
     st->done = 1;
   }

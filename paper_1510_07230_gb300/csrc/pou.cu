@@ -381,6 +381,7 @@ void enqueue_pass(pou_ctx* c) {
     g.sigma[k] = c->sigma[k];
   }
   g.trial = 1;
+  g.gate = 3;  // skipped on the intermediate steps of Algorithm M (n_org > 1)
   g.ng = c->ng;
   g.N = c->N;
   g.split = c->split;
@@ -390,6 +391,7 @@ void enqueue_pass(pou_ctx* c) {
   gram_layout<T>(c->ng, c->N, false, &nsplit, &npair, &chunk);
   GramReduceArgs r{};
   r.st = c->st;
+  r.gate = 3;
   r.split = c->split;
   r.nsplit = nsplit;
   r.npair = npair;
@@ -410,8 +412,8 @@ void enqueue_pass(pou_ctx* c) {
   }
   r.fp32_coef = 0;
   launch_gram_reduce(r, s);
-  // Cholesky and R^-1 in FP64
-  launch_cholinv(c->st, c->S, c->Rinv, c->N, nullptr, c->st, pivot_tol(c), reorth_thr(c), s);
+  // Cholesky and R^-1 in FP64 (R^-1 = I on the intermediate steps of Algorithm M)
+  launch_cholinv(c->st, c->S, c->Rinv, c->N, nullptr, c->st, pivot_tol(c), reorth_thr(c), s, true);
   // W_new = Wt R^-1 and rho into the other pair
   RotArgs<T> ra{};
   ra.rimg = c->rimg;
@@ -492,6 +494,7 @@ void enqueue_pass(pou_ctx* c) {
   k.bb_variant = c->cfg.bb_variant;
   k.max_backtrack = c->cfg.max_backtrack;
   k.n_diag = c->cfg.n_diag;
+  k.n_org = c->cfg.n_org;
   for (int q = 0; q < 3; ++q) k.kc[q] = -0.5 * stencil_scale(c, q);
   launch_control(k, s);
 }
@@ -849,7 +852,7 @@ pou_status pou_create(const pou_config* cfg, pou_ctx** out) {
   if (!(cfg->delta > 0.0 && cfg->delta < 1.0) || !(cfg->eta >= 0.0 && cfg->eta <= 1.0)) return POU_EINVAL;
   if (!(cfg->rho1 >= 0.0) || cfg->max_backtrack < 0 || cfg->max_backtrack > 60) return POU_EINVAL;
   if (!(cfg->tau_min > 0.0) || !(cfg->tau_max >= cfg->tau_min)) return POU_EINVAL;
-  if (cfg->n_org != 1 || cfg->n_diag < 0) return POU_EINVAL;
+  if (cfg->n_org < 1 || cfg->n_diag < 0) return POU_EINVAL;
   // N > 128: FP32 form only, without the subspace diagonalisation
   if (cfg->N > POU_MAX_N_FP64 && (cfg->precision != POU_FP32 || cfg->n_diag > 0)) return POU_EINVAL;
   const long long ng = (long long)cfg->n[0] * cfg->n[1] * cfg->n[2];

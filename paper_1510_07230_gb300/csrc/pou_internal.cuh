@@ -55,12 +55,17 @@ struct State {
   int reorth_count;  // second passes taken since the orbitals were set
   int diag_now;      // 1: subspace diagonalisation due before the next trial (Algorithm M)
   int diag_count;
+  int orth_now;      // 1: the next trial is orthonormalised (Algorithm M: every n_org steps)
 };
 
 // Gate of the optional kernels of a pass: 0 always run, 1 second Cholesky-QR
-// pass (State::reorth), 2 subspace diagonalisation (State::diag_now).
+// pass (State::reorth), 2 subspace diagonalisation (State::diag_now), 3 the
+// trial is orthonormalised (State::orth_now; Algorithm M with n_org > 1).
 __device__ __forceinline__ bool gate_open(const State* st, int gate) {
-  return gate == 0 || (gate == 1 ? st->reorth != 0 : st->diag_now != 0);
+  if (gate == 0) return true;
+  if (gate == 1) return st->reorth != 0;
+  if (gate == 2) return st->diag_now != 0;
+  return st->orth_now != 0;
 }
 
 // ---------------------------------------------------------------- stencil
@@ -182,7 +187,7 @@ void launch_scale_copy(const T* in, T* out, T scale, i64 n, cudaStream_t s);
 // reorth_thr > 0: first pass, sets st->reorth when max|S - I| > reorth_thr;
 // reorth_thr < 0: second pass, gated on st->reorth; 0: neither.
 void launch_cholinv(const State* st, const double* S, double* Rinv, int N, int* info,
-                    State* st_rw, double piv_rel, double reorth_thr, cudaStream_t s);
+                    State* st_rw, double piv_rel, double reorth_thr, cudaStream_t s, bool orth_gated = false);
 size_t cholinv_smem_bytes(int N);
 
 // ---------------------------------------------------------------- fft / potential
@@ -247,6 +252,7 @@ struct CtrlArgs {
   double dV, rho1, delta, eta, tau0, tau_min, tau_max;
   int bb_variant, max_backtrack;
   int n_diag;           // subspace diagonalisation period (0: off)
+  int n_org;            // Algorithm M: orthonormalise every n_org steps (1: every step)
   int refresh;          // 1: re-reduce the sums of the rotated current pair only
   int fp32;             // the H-apply formed z' = hw - sigma' w with sigma' rounded to FP32
   double kc[3];         // kinetic coefficient per axis: -1/2 * (1 or 1/12) / h_a^2

@@ -612,6 +612,50 @@ def test_subspace_diagonalisation_fp64_matches_oracle(P):
     s.close()
 
 
+# steps inside the chaos horizon: with U0 perturbed by 1e-15 the oracle's own
+# energies stay within 1e-11 for these many steps (n_org = 3: 3.7e-12 at 30
+# steps, 1.3e-8 at 36; n_org = 2: 4.6e-12 at 70)
+@pytest.mark.parametrize("n_org,n_diag,steps", [(2, 0, 70), (3, 0, 30), (2, 20, 70)])
+def test_algorithm_m_n_org_fp64_matches_oracle(P, n_org, n_diag, steps):
+    """Algorithm M with Orth every n_org steps (Sec. 3.3): the steps in
+    between take W - tau Z as it is; the energies of the orthonormalised steps
+    and the NaN entries of the others follow the oracle's trajectory."""
+    w, R, Z, U0, s = _workload_solver(P, "l10_g32_n4", n_org=n_org, n_diag=n_diag)
+    s.set_orbitals(U0)
+    s.iterate(steps)
+    Eg, taug = s.history()
+    cfg = ocfg(w.n, w.L, w.N, order=w.order, n_org=n_org, n_diag=n_diag)
+    vext = O.vext_gaussians(cfg, R, Z, w.width)
+    st = O.run(U0, vext, cfg, steps)
+    Eo = np.array([h.energy for h in st.history])
+    assert np.array_equal(np.isnan(Eg), np.isnan(Eo))
+    assert np.sum(np.isnan(Eo)) == steps - (steps + n_org - 1) // n_org
+    fin = ~np.isnan(Eo)
+    assert np.max(np.abs(Eg[fin] - Eo[fin])) <= 1e-9, np.max(np.abs(Eg[fin] - Eo[fin]))
+    np.testing.assert_allclose(taug, np.array([h.tau for h in st.history]), rtol=1e-6)
+    s.close()
+
+
+def test_algorithm_m_n_org_mixed_form(P):
+    """n_org = 2 in the mixed form: the orthonormalised steps reach the
+    oracle's converged energy region and the returned orbitals (taken after an
+    orthonormalised step) are orthonormal and carry the reported energy."""
+    w, R, Z, U0, s = _workload_solver(P, "l10_g32_n4", precision=1, n_org=2)
+    s.set_orbitals(U0)
+    s.iterate(2001)  # step l is orthonormalised when l % 2 == 0: the last one (l = 2000) is
+    E, _ = s.history()
+    fin = E[~np.isnan(E)]
+    assert len(fin) == 1001 and np.all(np.isfinite(fin))
+    Estar = _golden("l10_g32_n4")
+    assert abs(fin[-1] - Estar) < 1e-4  # the oracle is 2.0e-5 above E* after these 1000 Orth steps
+    W = s.get_orbitals()
+    cfg = ocfg(w.n, w.L, w.N, order=w.order)
+    assert np.max(np.abs(O.inner_matrix(W, W, cfg) - np.eye(w.N))) < 1e-6
+    vext = O.vext_gaussians(cfg, R, Z, w.width)
+    assert abs(O.energy(W, vext, cfg) - s.energy()["total"]) < 1e-7
+    s.close()
+
+
 @pytest.mark.parametrize("precision,tol", [(0, 1e-8), (1, 1e-6)])
 def test_algorithm_m_converged_energy(P, precision, tol):
     """Algorithm M (n_diag = 100, the paper's setting): both forms reach E*."""
