@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--ttt", action="store_true", help="time-to-1e-6 Ha, mixed vs FP64 (long)")
     ap.add_argument("--ttt-max", type=int, default=4000)
     ap.add_argument("--ttt-fp64-max", type=int, default=4000, help="cap of the FP64-alone run of --ttt")
+    ap.add_argument("--ttt-refine-max", type=int, default=4000, help="cap of the FP64 refinement of --ttt")
+    ap.add_argument("--ttt-conv-rel", type=float, default=1e-10,
+                    help="--ttt: the refinement stops when E falls by less than this times |E| over 100 steps")
     return ap.parse_args()
 
 
@@ -406,7 +409,7 @@ def time_to_tolerance(pou, torch, w, R, Z, U0, stream, args):
     """
     res = {}
     chunk = 50
-    switch_rel, conv_rel = 3e-8, 1e-10
+    switch_rel, conv_rel = 3e-8, args.ttt_conv_rel
 
     def stalled(rel):
         def f(E):  # energy drop over the last 100 steps
@@ -435,7 +438,7 @@ def time_to_tolerance(pou, torch, w, R, Z, U0, stream, args):
     s32, E32, t32 = run(pou.FP32, U0, args.ttt_max, stop=stalled(switch_rel))
     U = s32.get_orbitals()
     s32.close()
-    s64, E64b, t64b = run(pou.FP64, U, args.ttt_max, stop=stalled(conv_rel))
+    s64, E64b, t64b = run(pou.FP64, U, args.ttt_refine_max, stop=stalled(conv_rel))
     s64.close()
     E_ref = float(np.min(E64b))
     # 2. FP64 alone from the same start, until within 1e-6 Ha of the refined energy
@@ -469,8 +472,10 @@ def time_to_tolerance(pou, torch, w, R, Z, U0, stream, args):
         res["mixed_then_fp64"] = r
     res["E_star"] = Estar
     res["E_star_definition"] = ("lowest FP64-form energy: mixed form refined in FP64 until the energy falls by "
-                                f"less than {conv_rel:g} |E| over 100 steps ({len(E64b)} FP64 steps), and the FP64 "
-                                "form alone")
+                                f"less than {conv_rel:g} |E| over 100 steps or {args.ttt_refine_max} steps "
+                                f"({len(E64b)} FP64 steps run, last 100-step drop "
+                                f"{float(E64b[-101] - E64b[-1]) if len(E64b) > 100 else float('nan'):.3g} Ha), "
+                                "and the FP64 form alone")
     res["switch_rule"] = f"mixed energy falls by less than {switch_rel:g} |E| over 100 steps"
     res["workload"] = args.workload
     return res
