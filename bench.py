@@ -34,6 +34,14 @@ sys.path.insert(0, ROOT)
 from paper_1510_07230_gb300 import inputs  # noqa: E402
 
 METRIC = "outer iterations/s (160^3, N=128, 13-point, mixed form)"
+
+
+def metric_name(w, precision="fp32"):
+    """The metric line for a workload: the default one is the benchmark's."""
+    if w.name == "l30_g160_n128" and precision == "fp32":
+        return METRIC
+    form = "mixed form" if precision == "fp32" else "FP64 form"
+    return f"outer iterations/s ({w.n}^3, N={w.N}, {7 if w.order == 2 else 13}-point, {form})"
 UNIT = "iterations/s"
 
 
@@ -210,6 +218,7 @@ def run_oracle_sample(workload, ns, steps):
 
 def cpu_baseline(workload, steps=2, ns=8):
     w = inputs.WORKLOADS[workload]
+    ns = min(ns, w.N)
     times = run_oracle_sample(workload, ns, steps)
     per_iter = statistics.mean(times) * (w.N / ns)
     return {"value": 1.0 / per_iter, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -324,7 +333,7 @@ def run_ours(args):
             kernels[k]["gram_tflops"] = round(gram_flops(w.N, ng) / (t_ / eff / 1e3) / 1e12, 2)
     iter_kernels = [k for k in prof if k not in ("density", "forces", "potential_local", "convert", "scale_copy")]
     out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "metric": metric_name(w, args.precision), "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if prec == pou.FP32 else "f64", "data": "synthetic",
         "config": {"workload": args.workload, "grid": f"{w.n}^3", "L_bohr": w.L, "stencil_points": 7 if w.order == 2 else 13,
@@ -487,7 +496,7 @@ def run_reference(args):
     if rank != 0:
         return
     w = inputs.WORKLOADS[args.workload]
-    ns = 8
+    ns = min(8, w.N)
     total = args.warmup + args.steps
     times = run_oracle_sample(args.workload, ns, total)
     timed = times[args.warmup:]
@@ -495,7 +504,10 @@ def run_reference(args):
     value = 1.0 / per_iter
     sample = (f"each step: one oracle iteration on the first {ns} of the {w.N} orbitals of the "
               f"{w.n}^3 workload (FP64 NumPy, 1 BLAS thread), time scaled by {w.N}/{ns}")
-    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+    # n_gpus: the launch's GPU count (the line pairs with our arm's); the
+    # oracle itself runs on one host core, as cpu_baseline says
+    out = {"impl": "reference", "metric": metric_name(w, args.precision), "value": value, "unit": UNIT,
+           "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_iter * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": {"workload": args.workload, "grid": f"{w.n}^3", "N": w.N},

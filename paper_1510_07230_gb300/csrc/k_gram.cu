@@ -228,19 +228,15 @@ __global__ void k_gram_reduce(GramReduceArgs a) {
   }
   s *= a.dV;
   if (a.trial && r == c) {
-    // FP64 norm of the trial column a w - t hw (a, t: the coefficients as the
-    // kernels round them) from the H-apply sums of W[cur]:
+    // FP64 norm of the trial column a w - t hw (FP64 coefficients, as both
+    // rotations form the trial point) from the H-apply sums of W[cur]:
     //   a w - t hw = w - t z_e,  z_e = hw - s_e w,  s_e = (a - 1) / t,
     //   z_e = z' - d w with z' = hw - sigma' w, d = s_e - sigma',
     //   ||w - t z_e||^2 = <w,w> - 2 t <w,z_e> + t^2 <z_e,z_e>.
     const int cur = a.st->cur;
     const double tau = a.st->tau_trial;
-    double coef = 1.0 + tau * a.sigma[cur][r];
-    double t = tau;
-    if (a.fp32_coef) {
-      coef = (double)(float)coef;
-      t = (double)(float)tau;
-    }
+    const double coef = 1.0 + tau * a.sigma[cur][r];
+    const double t = tau;
     const double* pp = a.part[cur] + (i64)r * NP;
     const double d = (coef - 1.0) / t - pp[P_SIGP];
     const double wz = pp[P_ZW] - d * pp[P_WW];

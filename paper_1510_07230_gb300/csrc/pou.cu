@@ -410,7 +410,6 @@ void enqueue_pass(pou_ctx* c) {
     r.sigma[k] = c->sigma[k];
     r.part[k] = c->part[k];
   }
-  r.fp32_coef = 0;
   launch_gram_reduce(r, s);
   // Cholesky and R^-1 in FP64 (R^-1 = I on the intermediate steps of Algorithm M)
   launch_cholinv(c->st, c->S, c->Rinv, c->N, nullptr, c->st, pivot_tol(c), reorth_thr(c), s, true);

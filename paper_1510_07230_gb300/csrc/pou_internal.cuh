@@ -134,7 +134,6 @@ struct GramReduceArgs {
   int trial;
   const double* sigma[2];
   const double* part[2];
-  int fp32_coef;        // coefficients rounded to FP32 as in the FP32 kernels
   int gate;             // see gate_open
 };
 void launch_gram_reduce(const GramReduceArgs& a, cudaStream_t s);

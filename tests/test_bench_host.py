@@ -88,3 +88,27 @@ def test_traffic_scales_with_units_and_checks_the_source():
         pytest.skip("no committed traffic entry for the current H-apply source")
     assert bench.traffic_for("apply_h", 2000) == pytest.approx(2 * t1)
     assert bench.traffic_for("no_such_kernel", 1000) is None
+
+
+def test_reference_arm_line_keeps_the_contract():
+    """The reference arm (the oracle, timed on a host core) prints one JSON
+    line with the keys of the bench contract, for the workload it was given."""
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                        "--warmup", "1", "--workload", "l10_g32_n4"], capture_output=True, text=True, cwd=ROOT,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 1 and d["value"] > 0
+    assert d["metric"].startswith("outer iterations/s (32^3, N=4")
+    assert d["config"]["workload"] == "l10_g32_n4"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert "first 4 of the 4 orbitals" in d["cpu_baseline"]["sample"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    assert d["ms_per_step"] == pytest.approx(1e3 / d["value"])
