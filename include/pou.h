@@ -100,7 +100,7 @@ typedef struct {
 } pou_config;
 
 #define POU_MAX_N 512      /* FP32 form (without the subspace diagonalisation) */
-#define POU_MAX_N_FP64 128 /* FP64 form, the subspace diagonalisation, pou_gradient_norm, FP64 pou_rotate */
+#define POU_MAX_N_FP64 128 /* FP64 form, the subspace diagonalisation, FP64 pou_rotate */
 
 typedef struct {
   double kinetic;   /* f sum_i <w_i, -1/2 Lap_h w_i> */
@@ -180,8 +180,7 @@ pou_status pou_get_potential(pou_ctx* ctx, double* V, int on_device);
  * (host).  Sigma is formed on the device in the working precision; G is
  * formed point by point and its squares summed in FP64.  Synchronises the
  * context's stream.  POU_EINVAL when no orbitals are set.  Overwrites the
- * context's N x N scratch matrix (not part of the iteration state).  N <= POU_MAX_N_FP64
- * (POU_EINVAL above). */
+ * context's N x N scratch matrix (not part of the iteration state).  */
 pou_status pou_gradient_norm(pou_ctx* ctx, double* out);
 
 /* Energy of an arbitrary block U (not orthonormalised, Eq. energy) without

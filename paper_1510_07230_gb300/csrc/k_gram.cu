@@ -532,70 +532,82 @@ __global__ void __launch_bounds__(RNT) k_rotate_f32_cc(RotArgs<float> a, int nch
 // (Eq. gra): G = HW - W Sigma with Sigma_ij = <hw_i, w_j>, so that
 // g_i = hw_i - sum_j Sigma_ji w_j, and ||G||_F^2 = dV sum_i sum_p g_i(p)^2.
 // Sig is the general Gram S_ij = <w_i, hw_j> = Sigma_ji.
-// G is formed point by point (a chunk of RP points of all orbitals staged in
-// shared memory, 8 orbitals x 4 points per thread, working-type FMAs): near
-// convergence g is a small difference of O(1) terms, which the trace identity
-// tr(HW^T HW) - |Sigma|^2 would lose to cancellation.  Each CTA writes one
-// FP64 partial of sum g^2.
+// G is formed point by point (a chunk of RP points staged in shared memory,
+// 8 orbitals x 4 points per thread, working-type FMAs): near convergence g
+// is a small difference of O(1) terms, which the trace identity
+// tr(HW^T HW) - |Sigma|^2 would lose to cancellation.  Orbitals are taken in
+// blocks of 128 (Sigma one 128 x 128 tile at a time for N > 128).  Each CTA
+// writes one FP64 partial of sum g^2.
 template <typename T>
 __global__ void __launch_bounds__(RNT) k_residual(const T* W, const T* HW, const double* Sig, int N, i64 ng,
                                                    int nchunks, double* part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int NPAD = 128;
-  T* Ss = reinterpret_cast<T*>(smem_raw);  // [NPAD][NPAD]: Ss[j][i] = S_ij = Sigma_ji
-  T* Xs = Ss + NPAD * NPAD;                // [NPAD][RP + 4] chunk of W
+  T* Ss = reinterpret_cast<T*>(smem_raw);  // [NPAD][NPAD]: Ss[j][i] = S_(ib+i)(jb+j) = Sigma_ji
+  T* Xs = Ss + NPAD * NPAD;                // [NPAD][RP + 4] chunk of W, rows jb ..
   constexpr int XS = RP + 4;
   __shared__ double red[RNT / 32];
   const int tid = threadIdx.x;
-  for (int idx = tid; idx < NPAD * NPAD; idx += RNT) {
-    const int j = idx / NPAD, i = idx % NPAD;
-    Ss[idx] = (i < N && j < N) ? (T)Sig[(i64)i * N + j] : T(0);
-  }
+  const int nb = (N + NPAD - 1) / NPAD;
+  auto load_sig = [&](int ib, int jb) {
+    for (int idx = tid; idx < NPAD * NPAD; idx += RNT) {
+      const int j = idx / NPAD, i = idx % NPAD;
+      const int gi = ib * NPAD + i, gj = jb * NPAD + j;
+      Ss[idx] = (gi < N && gj < N) ? (T)Sig[(i64)gi * N + gj] : T(0);
+    }
+  };
+  if (nb == 1) load_sig(0, 0);
   const int lane = tid & 31, warp = tid >> 5;
   const int iw = warp & 3, pw = warp >> 2;
   const int ig = lane & 3, pg = lane >> 2;
-  const int i0 = iw * 32 + ig * 8;   // 8 orbitals
+  const int i0 = iw * 32 + ig * 8;   // 8 orbitals of the block
   const int pl0 = pw * 32 + pg * 4;  // 4 points within the chunk
   double total = 0.0;
   for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const i64 p0 = (i64)ch * RP;
-    __syncthreads();
-    for (int idx = tid; idx < N * RP; idx += RNT) {
-      const int j = idx / RP, pp = idx % RP;
-      const i64 gp = p0 + pp;
-      Xs[j * XS + pp] = gp < ng ? W[(i64)j * ng + gp] : T(0);
-    }
-    __syncthreads();
-    T acc[8][4];
-#pragma unroll
-    for (int ii = 0; ii < 8; ++ii)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[ii][q] = T(0);
-    for (int j = 0; j < N; ++j) {
-      T sv[8], xv[4];
-#pragma unroll
-      for (int ii = 0; ii < 8; ++ii) sv[ii] = Ss[j * NPAD + i0 + ii];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) xv[q] = Xs[j * XS + pl0 + q];
+    for (int ib = 0; ib < nb; ++ib) {
+      T acc[8][4];
 #pragma unroll
       for (int ii = 0; ii < 8; ++ii)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[ii][q] = fma(sv[ii], xv[q], acc[ii][q]);
-    }
-    double part_sum = 0.0;
+        for (int q = 0; q < 4; ++q) acc[ii][q] = T(0);
+      for (int jb = 0; jb < nb; ++jb) {
+        const int nj = min(NPAD, N - jb * NPAD);
+        __syncthreads();
+        if (nb > 1) load_sig(ib, jb);
+        for (int idx = tid; idx < nj * RP; idx += RNT) {
+          const int j = idx / RP, pp = idx % RP;
+          const i64 gp = p0 + pp;
+          Xs[j * XS + pp] = gp < ng ? W[(i64)(jb * NPAD + j) * ng + gp] : T(0);
+        }
+        __syncthreads();
+        for (int j = 0; j < nj; ++j) {
+          T sv[8], xv[4];
 #pragma unroll
-    for (int ii = 0; ii < 8; ++ii) {
-      const int i = i0 + ii;
-      if (i >= N) continue;
+          for (int ii = 0; ii < 8; ++ii) sv[ii] = Ss[j * NPAD + i0 + ii];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const i64 gp = p0 + pl0 + q;
-        if (gp >= ng) continue;
-        const T g = HW[(i64)i * ng + gp] - acc[ii][q];
-        part_sum += (double)g * (double)g;
+          for (int q = 0; q < 4; ++q) xv[q] = Xs[j * XS + pl0 + q];
+#pragma unroll
+          for (int ii = 0; ii < 8; ++ii)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[ii][q] = fma(sv[ii], xv[q], acc[ii][q]);
+        }
       }
+      double part_sum = 0.0;
+#pragma unroll
+      for (int ii = 0; ii < 8; ++ii) {
+        const int i = ib * NPAD + i0 + ii;
+        if (i >= N) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const i64 gp = p0 + pl0 + q;
+          if (gp >= ng) continue;
+          const T g = HW[(i64)i * ng + gp] - acc[ii][q];
+          part_sum += (double)g * (double)g;
+        }
+      }
+      total += part_sum;
     }
-    total += part_sum;
   }
   for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
   if (lane == 0) red[warp] = total;

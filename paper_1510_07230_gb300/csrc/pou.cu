@@ -1216,7 +1216,6 @@ pou_status pou_gradient_norm(pou_ctx* c, double* out) {
   ProfScope prof_scope(c);
   if (!c || !out) return fail(c, POU_EINVAL, "bad argument");
   if (!c->have_orbitals) return fail(c, POU_EINVAL, "no orbitals set");
-  if (c->N > POU_MAX_N_FP64) return fail(c, POU_EINVAL, "gradient norm: N > %d not built", POU_MAX_N_FP64);
   int cur;
   pou_status e = cur_index(c, &cur);
   if (e != POU_OK) return e;

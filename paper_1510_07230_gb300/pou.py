@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "POU_OK", 1: "POU_EINVAL", 2: "POU_ENOMEM", 3: "POU_ECUDA", 4
 FP64, FP32 = 0, 1
 DT_F64, DT_F32 = 0, 1
 MAX_N = 512       # FP32 form
-MAX_N_FP64 = 128  # FP64 form, subspace diagonalisation, gradient norm
+MAX_N_FP64 = 128  # FP64 form, subspace diagonalisation
 
 
 class PouError(RuntimeError):
