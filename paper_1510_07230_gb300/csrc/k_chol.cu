@@ -500,6 +500,8 @@ __global__ void __launch_bounds__(256) k_big_final(BigArgs a, int* info) {
 
 void launch_cholinv_big(const State* st, const double* S, double* Rinv, int N, int* info, State* st_rw,
                         double piv_rel, double reorth_thr, cudaStream_t s, bool orth_gated) {
+  // the failing-pivot flag: the caller's info, else the iteration state's chol_info
+  if (!info && !st_rw) return;
   BigArgs a{st, st_rw, S, Rinv, N, info ? info : &st_rw->chol_info, piv_rel, reorth_thr, orth_gated ? 1 : 0};
   const int np = (N + BT - 1) / BT;
   k_big_init<<<1, 1024, 0, s>>>(a);
