@@ -31,6 +31,11 @@ diagonalisation; Sec. 3.2):
    W(tau) = Orth(W - tau Z), Orth = Cholesky-based QR
 4. Q^(l+1) = eta Q^l + 1, C^(l+1) = (eta Q^l C^l + E^(l+1)) / Q^(l+1)
 
+Algorithm M options (Sec. 3.3): n_org > 1 orthonormalises only the steps
+l = 0 mod n_org (the others take W - tau Z as it is, without the test of
+step 3; C, Q and E are kept); n_diag > 0 rotates W to the eigenvectors of
+Sigma = <W^T H W> after every n_diag-th orthonormalised step.
+
 Readings where the paper is silent (also listed in the design notes):
 the two BB steps ("tau1 or tau2") alternate by default, tau1 on even l;
 tau at l = 0 and when tr<S^T Y> = 0 is 1 / lambda_max(-1/2 Lap_h); tau is

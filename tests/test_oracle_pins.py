@@ -391,6 +391,28 @@ def test_algorithm_m_variants_reach_same_energy():
     assert abs(a.E - b.E) < 1e-8
 
 
+@pytest.mark.parametrize("n_org", [2, 3])
+def test_algorithm_m_n_org_same_minimum_and_structure(n_org):
+    """Algorithm M with Orth every n_org steps (Sec. 3.3) reaches the minimum
+    Algorithm E reaches; only steps l = 0 mod n_org are orthonormalised (their
+    iterates are orthonormal, the others carry no energy)."""
+    cfg = O.cubic(10, 7.0, order=2, N=4)
+    R, Z = inputs.atoms(41, 2, 7.0, "const4")
+    vext = O.vext_gaussians(cfg, R, Z, 0.8)
+    U0 = inputs.random_orbitals(41, 4, cfg.n)
+    a = O.run(U0, vext, cfg, 3000, e_tol=1e-16)
+    cfgm = O.cubic(10, 7.0, order=2, N=4, n_org=n_org)
+    b = O.run(U0, vext, cfgm, 6000, e_tol=1e-16)
+    assert abs(b.E - a.E) < 1e-10
+    E = np.array([h.energy for h in b.history])
+    assert np.array_equal(np.isfinite(E), np.arange(len(E)) % n_org == 0)
+    st = O.initial_state(U0, vext, cfgm)
+    for l in range(3 * n_org):
+        O.iterate(st, vext, cfgm)
+        if st.l % n_org == 1 or n_org == 1:  # the step just taken (l - 1) was orthonormalised
+            assert np.max(np.abs(O.inner_matrix(st.W, st.W, cfgm) - np.eye(4))) < 1e-12
+
+
 @pytest.mark.slow
 def test_bb_trajectory_is_chaotic():
     """A 1e-15 relative change of U0 moves the oracle's energy by > 1e-8 within 200 steps
