@@ -11,9 +11,11 @@
 // points through the ring, so that every producer thread still holds four
 // rows of one block at a time.
 //
-// Precision: every FP32 value x of the block is split into hi = tf32(x) and
-// lo = x - hi (exact in FP32); the tensor core reads the leading TF32 bits of
-// lo (truncation), so x = hi + lo + O(2^-22 x), the same split the
+// Precision: every value x of the block is split into hi = tf32(x) and
+// lo = x - hi (exact in FP32 for a plain block; for the trial block x is
+// formed from the FP64 coefficients as a double-float and lo is its
+// remainder rounded once); the tensor core reads the leading TF32 bits of lo
+// (truncation), so x = hi + lo + O(2^-22 x), bit for bit the split the
 // tensor-core rotation applies to the block it rotates.  On a diagonal block
 // two MMAs of shape M = N = 128, K = 8 per K step accumulate
 // D += Hi Hi^T + Hi (2 Lo)^T, so that the symmetric part
@@ -26,7 +28,9 @@
 // partial is added into a compensated pair (sum, error) that also lives in
 // tensor memory (TwoSum, round to nearest).  The diagonal, the one entry
 // whose products all have one sign, is summed exactly on the CUDA cores from
-// the FP32 values (double-float) and replaces the tensor-core diagonal.
+// the FP32 values (double-float) and replaces the tensor-core diagonal; for
+// the trial block the reduction replaces it with the FP64 norm from the
+// H-apply sums instead.
 //
 // Roles (one CTA per SM, 416 threads: 13 warps, at most four per SM
 // sub-partition, so that each thread may hold 128 registers):

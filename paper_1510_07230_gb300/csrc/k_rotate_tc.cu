@@ -1,13 +1,14 @@
 // Rotation W_new = Wt R^-1 of the FP32 form (Orth by Cholesky-QR, Sec. 3.2)
 // on the 5th-generation tensor cores, fused with the density
-// rho = f sum_j w_new_j^2 (Sec. 2), for N <= 128 orbitals and upper
-// triangular R^-1 (the dense subspace rotation of Algorithm M runs on the CUDA
-// cores).
+// rho = f sum_j w_new_j^2 (Sec. 2), for N <= 128 orbitals (k_rotate_tc; up to
+// 512 with k_rotate_tc_big further below) and upper triangular R^-1 (the
+// dense subspace rotation of Algorithm M runs on the CUDA cores).
 //
 // Split of the work.  Output j at point p is
 //   w_new_j(p) = sum_{i < j} x_i(p) R_ij  +  R_jj x_j(p),
-// x = Wt (trial: (1 + tau sigma_i) w_i - tau hw_i, rounded once to FP32, the
-// same value the trial Gram matrix is formed from) or the block itself.  The
+// x = Wt (trial: (1 + tau sigma_i) w_i - tau hw_i from the FP64 coefficients,
+// formed as a double-float exactly as the trial Gram matrix forms it) or the
+// block itself.  The
 // off-diagonal sum runs on the tensor cores as D = X R_off with M = 128 grid
 // points (tensor-memory lanes), N = outputs j (columns) and K = orbitals i,
 // both operands split into TF32 pairs: D = Xhi Rhi + Xhi Rlo + Xlo Rhi, which
@@ -24,9 +25,10 @@
 // that keep each orbital normalised are below half an ulp of its elements.
 //
 // The whole 128-point X tile stays in shared memory (four atom slots) until
-// the epilogue has used it: Xhi = tf32(x) and Xlo = x - Xhi (exact in FP32;
-// the tensor core reads its leading TF32 bits), so that x = Xhi + Xlo is
-// available to the self term without reading w and hw again.
+// the epilogue has used it: Xhi = tf32(x) and Xlo = x - Xhi (exact in FP32
+// for a plain block, rounded once from the double-float trial point; the
+// tensor core reads its leading TF32 bits), so that x = Xhi + Xlo (35 bits)
+// is available to the self term without reading w and hw again.
 //
 // With points on the lanes, every global access of the epilogue (the output,
 // the density) is one 128-byte segment of one row per warp instruction, and
