@@ -4,7 +4,7 @@
  * Method: Dai, Liu, Zhang, Zhou, "A Parallel Orbital-updating Based
  * Optimization Method for Electronic Structure Calculations" (arXiv 1510.07230).
  *
- * Problem statement (Sec. 2.1, Eq. emin and Eq. energy; Algorithm B step 1):
+ * Problem statement (Sec. 2.1, Eq. emin and Eq. energy; the initialisation of Algorithm B):
  * given a uniform periodic grid, the external potential (or Gaussian-well
  * atoms), the number N of doubly occupied orbitals and an initial block U,
  * minimise the discrete Kohn-Sham energy
@@ -150,7 +150,7 @@ pou_status pou_set_vext(pou_ctx* ctx, const double* vext, int on_device);
  * doubles (x, y, z per atom), Z: M host doubles; width > 0. */
 pou_status pou_set_atoms(pou_ctx* ctx, int M, const double* R, const double* Z, double width);
 
-/* Load N orbitals (Algorithm B step 1) and orthonormalise them by one
+/* Load N orbitals (the initialisation of Algorithm B) and orthonormalise them by one
  * Cholesky-QR; then build rho, V and E of the orthonormal block and reset
  * the iteration history (C^0 = E, Q^0 = 1, Sec. 3.2).  U: [N][nz][ny][nx]
  * in dtype.  ENOTSPD if U is rank deficient. */

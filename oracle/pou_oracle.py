@@ -328,7 +328,7 @@ class State:
 
 
 def initial_state(U0: np.ndarray, vext: np.ndarray, cfg: Config) -> State:
-    """Algorithm B step 1: orthonormalise U0, then C^0 = E(W^0), Q^0 = 1 (Sec. 3.2)."""
+    """Initialisation of Algorithm B: orthonormalise U0, then C^0 = E(W^0), Q^0 = 1 (Sec. 3.2)."""
     W, _, _ = cholesky_qr(np.asarray(U0, dtype=np.float64), cfg)
     rho = density(W)
     V = total_potential(rho, vext, cfg)

@@ -498,7 +498,7 @@ void enqueue_pass(pou_ctx* c) {
   launch_control(k, s);
 }
 
-// Orthonormalise the block staged in W[0], build rho, V, HW, E (Algorithm B step 1).
+// Orthonormalise the block staged in W[0], build rho, V, HW, E (the initialisation of Algorithm B).
 template <typename T>
 pou_status init_from_staged(pou_ctx* c) {
   cudaStream_t s = c->stream;
