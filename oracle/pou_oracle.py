@@ -33,7 +33,7 @@ diagonalisation; Sec. 3.2):
 
 Algorithm M options (Sec. 3.3): n_org > 1 orthonormalises only the steps
 l = 0 mod n_org (the others take W - tau Z as it is, without the test of
-step 3; C, Q and E are kept); n_diag > 0 rotates W to the eigenvectors of
+the Eq. (ene-de) test; C, Q and E are kept); n_diag > 0 rotates W to the eigenvectors of
 Sigma = <W^T H W> after every n_diag-th orthonormalised step.
 
 Readings where the paper is silent (also listed in the design notes):
