@@ -32,8 +32,8 @@ diagonalisation; Sec. 3.2):
 4. Q^(l+1) = eta Q^l + 1, C^(l+1) = (eta Q^l C^l + E^(l+1)) / Q^(l+1)
 
 Algorithm M options (Sec. 3.3): n_org > 1 orthonormalises only the steps
-l = 0 mod n_org (the others take W - tau Z as it is, without the test of
-the Eq. (ene-de) test; C, Q and E are kept); n_diag > 0 rotates W to the eigenvectors of
+l = 0 mod n_org (the others take W - tau Z as it is, without the Eq. (ene-de)
+test; C, Q and E are kept); n_diag > 0 rotates W to the eigenvectors of
 Sigma = <W^T H W> after every n_diag-th orthonormalised step.
 
 Readings where the paper is silent (also listed in the design notes):
