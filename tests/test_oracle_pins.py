@@ -99,6 +99,18 @@ def test_random_orbitals_prefix_is_the_same_draw():
     assert np.array_equal(a[:2], b)
 
 
+def test_random_orbitals_float32_draw():
+    """The float32 draw (for blocks too large to draw in float64) is seeded,
+    orbital by orbital, so a prefix is the same draw, and it is a standard
+    normal sample."""
+    a = inputs.random_orbitals(7, 5, (9, 8, 7), dtype=np.float32)
+    b = inputs.random_orbitals(7, 5, (9, 8, 7), dtype=np.float32)
+    c = inputs.random_orbitals(7, 5, (9, 8, 7), count=2, dtype=np.float32)
+    assert a.dtype == np.float32 and a.shape == (5, 7, 8, 9)
+    assert np.array_equal(a, b) and np.array_equal(a[:2], c)
+    assert abs(float(np.mean(a))) < 0.05 and abs(float(np.std(a)) - 1.0) < 0.05
+
+
 def test_hartree_cosine_closed_form():
     cfg = O.Config(n=(16, 12, 10), L=(7.0, 6.0, 5.0))
     x, y, z = O.grid_coords(cfg)
