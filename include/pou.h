@@ -231,7 +231,10 @@ pou_status pou_get_profile(pou_ctx* ctx, int max_entries, char* names, long long
 /* ------------------------------------------------------------------------
  * Stand-alone operations on caller-owned device buffers.  These run the
  * same kernels as the iteration, one step of Sec. 3.2 each.  Pointers are
- * device pointers, stream is a cudaStream_t (NULL = legacy default stream).
+ * device pointers (a pointer that is not CUDA device or managed memory
+ * returns POU_EINVAL before any launch; so does on_device = 1 with such a
+ * pointer in the calls above), stream is a cudaStream_t (NULL = legacy
+ * default stream).
  * ------------------------------------------------------------------------ */
 
 /* Gram matrix S = dV * A^T A (Sec. 3.2, Cholesky-based QR, first step) of a

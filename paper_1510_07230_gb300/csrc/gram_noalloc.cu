@@ -87,6 +87,7 @@ extern "C" pou_status pou_gram_noalloc(int dtype, long long Ng, int N, const voi
                                        void* stream) {
   if ((dtype != POU_DT_F64 && dtype != POU_DT_F32) || Ng < 1 || N < 1 || N > POU_MAX_N || !A || !S)
     return POU_EINVAL;
+  if (!pou::device_accessible(A) || !pou::device_accessible(S)) return POU_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (dtype == POU_DT_F64) return gram_noalloc<double>(Ng, N, A, dV, S, s);
   return gram_noalloc<float>(Ng, N, A, dV, S, s);

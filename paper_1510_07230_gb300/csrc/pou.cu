@@ -606,6 +606,7 @@ pou_status init_from_staged(pou_ctx* c) {
 
 pou_status stage_block(pou_ctx* c, const void* U, int dtype, int on_device, void* dst) {
   const size_t n = (size_t)c->N * (size_t)c->ng;
+  if (on_device && !device_accessible(U)) return fail(c, POU_EINVAL, "on_device = 1 but not device memory");
   if (dtype == c->dt) {
     CK(cudaMemcpyAsync(dst, U, n * c->esz, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                        c->stream));
@@ -636,6 +637,7 @@ pou_status stage_block(pou_ctx* c, const void* U, int dtype, int on_device, void
 
 pou_status unstage_block(pou_ctx* c, const void* src, void* U, int dtype, int on_device) {
   const size_t n = (size_t)c->N * (size_t)c->ng;
+  if (on_device && !device_accessible(U)) return fail(c, POU_EINVAL, "on_device = 1 but not device memory");
   if (dtype == c->dt) {
     CK(cudaMemcpyAsync(U, src, n * c->esz, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                        c->stream));
@@ -975,6 +977,7 @@ const char* pou_last_error(const pou_ctx* c) { return c ? c->err.c_str() : "null
 
 pou_status pou_set_vext(pou_ctx* c, const double* vext, int on_device) {
   if (!c || !vext) return fail(c, POU_EINVAL, "null argument");
+  if (on_device && !device_accessible(vext)) return fail(c, POU_EINVAL, "on_device = 1 but not device memory");
   CK(cudaMemcpyAsync(c->vext, vext, c->ng * sizeof(double),
                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));
@@ -1150,6 +1153,7 @@ pou_status pou_get_orbitals(pou_ctx* c, void* U, int dtype, int on_device) {
 
 pou_status pou_get_density(pou_ctx* c, double* rho, int on_device) {
   if (!c || !rho) return POU_EINVAL;
+  if (on_device && !device_accessible(rho)) return fail(c, POU_EINVAL, "on_device = 1 but not device memory");
   if (!c->have_orbitals) return fail(c, POU_EINVAL, "no orbitals");
   int cur;
   pou_status e = cur_index(c, &cur);
@@ -1162,6 +1166,7 @@ pou_status pou_get_density(pou_ctx* c, double* rho, int on_device) {
 
 pou_status pou_get_potential(pou_ctx* c, double* V, int on_device) {
   if (!c || !V) return POU_EINVAL;
+  if (on_device && !device_accessible(V)) return fail(c, POU_EINVAL, "on_device = 1 but not device memory");
   if (!c->have_orbitals) return fail(c, POU_EINVAL, "no orbitals");
   int cur;
   pou_status e = cur_index(c, &cur);
@@ -1228,6 +1233,7 @@ pou_status pou_evaluate(pou_ctx* c, const void* U, int dtype, int on_device, pou
   pou_status e = ensure_eval_buffers(c);
   if (e != POU_OK) return e;
   const void* src = U;
+  if (on_device && !device_accessible(U)) return fail(c, POU_EINVAL, "on_device = 1 but not device memory");
   if (!(on_device && dtype == c->dt)) {
     e = stage_block(c, U, dtype, on_device, c->ublock);
     if (e != POU_OK) return e;
@@ -1255,6 +1261,7 @@ pou_status pou_backward(pou_ctx* c, const void* U, int dtype, int on_device, dou
     src = c->W[cur];
     out_dt = (dtype == POU_DT_F64 || dtype == POU_DT_F32) ? dtype : c->dt;
   } else if (on_device && dtype == c->dt) {
+    if (!device_accessible(U)) return fail(c, POU_EINVAL, "on_device = 1 but not device memory");
     src = U;
   } else {
     e = stage_block(c, U, dtype, on_device, c->ublock);
@@ -1262,6 +1269,8 @@ pou_status pou_backward(pou_ctx* c, const void* U, int dtype, int on_device, dou
     src = c->ublock;
   }
   const double scale = g * 2.0 * F_OCC * c->dV;
+  if (dEdU && on_device && !device_accessible(dEdU))
+    return fail(c, POU_EINVAL, "on_device = 1 but dEdU is not device memory");
   const bool direct = dEdU && on_device && out_dt == c->dt;
   void* gout = dEdU ? (direct ? dEdU : c->gblock) : nullptr;
   if (c->dt == 0)
@@ -1464,6 +1473,7 @@ pou_status pou_gram(int dtype, long long Ng, int N, const void* A, double dV, do
       !workspace)
     return POU_EINVAL;
   if (workspace_bytes < pou_gram_workspace_bytes(dtype, Ng, N)) return POU_EINVAL;
+  if (!device_accessible(A) || !device_accessible(S) || !device_accessible(workspace)) return POU_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int nsplit, npair;
   i64 chunk;
@@ -1500,6 +1510,7 @@ pou_status pou_gram(int dtype, long long Ng, int N, const void* A, double dV, do
 pou_status pou_cholinv(int N, const double* S, double* Rinv, int* info, void* stream) {
   configure_kernels();
   if (N < 1 || N > POU_MAX_N || !S || !Rinv || !info) return POU_EINVAL;
+  if (!device_accessible(S) || !device_accessible(Rinv) || !device_accessible(info)) return POU_EINVAL;
   launch_cholinv(nullptr, S, Rinv, N, info, nullptr, 0.0, 0.0, static_cast<cudaStream_t>(stream));
   return cudaGetLastError() == cudaSuccess ? POU_OK : POU_ECUDA;
 }
@@ -1510,6 +1521,9 @@ pou_status pou_rotate(int dtype, long long Ng, int N, const void* A, const doubl
   if ((dtype != POU_DT_F64 && dtype != POU_DT_F32) || Ng < 1 || N < 1 || N > POU_MAX_N || !A || !Rinv || !B)
     return POU_EINVAL;
   if (dtype == POU_DT_F64 && N > POU_MAX_N_FP64) return POU_EINVAL;
+  if (!device_accessible(A) || !device_accessible(Rinv) || !device_accessible(B) ||
+      (rho && !device_accessible(rho)))
+    return POU_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (dtype == POU_DT_F64) {
     RotArgs<double> ra{};
@@ -1551,6 +1565,7 @@ pou_status pou_hartree(const int n[3], const double L[3], const double* rho, dou
   for (int a = 0; a < 3; ++a)
     if (n[a] < 1 || !fft_supported(n[a]) || !(L[a] > 0.0)) return POU_EINVAL;
   if (workspace_bytes < pou_hartree_workspace_bytes(n)) return POU_EINVAL;
+  if (!device_accessible(rho) || !device_accessible(vh) || !device_accessible(workspace)) return POU_EINVAL;
   FftPlan p{};
   if (fft_plan_create(&p, n, L) != 0) {
     fft_plan_destroy(&p);
@@ -1570,3 +1585,15 @@ pou_status pou_hartree(const int n[3], const double L[3], const double* rho, dou
 }
 
 }  // extern "C"
+
+namespace pou {
+bool device_accessible(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+}  // namespace pou

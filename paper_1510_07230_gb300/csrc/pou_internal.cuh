@@ -258,6 +258,11 @@ struct CtrlArgs {
 };
 void launch_control(const CtrlArgs& a, cudaStream_t s);
 
+// true if p is CUDA device (or managed) memory of this process; the entry
+// points that take device pointers check them, so that a host pointer gives
+// POU_EINVAL instead of reaching a kernel
+bool device_accessible(const void* p);
+
 // Shared-memory opt-ins of the kernels that need more than 48 KB; called
 // once per process before any launch (and before any graph capture).
 void configure_rotate();

@@ -347,27 +347,47 @@ class Solver:
 
 
 # ------------------------------------------------------------ stand-alone ops
+def _dev(x, what, dtype=None, numel=None):
+    """Device pointer of a contiguous CUDA tensor, checked before the call
+    (the library also refuses host pointers where it expects device memory)."""
+    if not _is_torch(x) or not x.is_cuda:
+        raise ValueError(f"{what}: a CUDA tensor is required")
+    if not x.is_contiguous():
+        raise ValueError(f"{what}: tensor must be contiguous")
+    if dtype is not None and x.dtype != dtype:
+        raise TypeError(f"{what}: dtype {x.dtype}, expected {dtype}")
+    if numel is not None and x.numel() < numel:
+        raise ValueError(f"{what}: {x.numel()} elements, need {numel}")
+    return C.c_void_p(x.data_ptr())
+
+
 def _stream_ptr(stream):
     return C.c_void_p(int(stream)) if stream is not None else C.c_void_p()
 
 
 def gram(A, dV, S, workspace, stream=None):
     """S = dV A^T A for a device block A [N][Ng] (torch tensors on CUDA)."""
+    import torch
+    _dev(A, "A")
     N = A.shape[0]
     ng = A.numel() // N
     p, dt, _ = _ptr(A)
-    st = _lib.pou_gram(dt, ng, N, p, float(dV), C.c_void_p(S.data_ptr()), C.c_void_p(workspace.data_ptr()),
-                       workspace.numel() * workspace.element_size(), _stream_ptr(stream))
+    sp = _dev(S, "S", torch.float64, N * N)
+    wp = _dev(workspace, "workspace")
+    st = _lib.pou_gram(dt, ng, N, p, float(dV), sp, wp, workspace.numel() * workspace.element_size(),
+                       _stream_ptr(stream))
     if st != OK:
         raise PouError(st, "pou_gram")
 
 
 def gram_noalloc(A, dV, S, stream=None):
     """S = dV A^T A like gram(), with no workspace: the library's fixed device buffer."""
+    import torch
+    _dev(A, "A")
     N = A.shape[0]
     ng = A.numel() // N
     p, dt, _ = _ptr(A)
-    st = _lib.pou_gram_noalloc(dt, ng, N, p, float(dV), C.c_void_p(S.data_ptr()), _stream_ptr(stream))
+    st = _lib.pou_gram_noalloc(dt, ng, N, p, float(dV), _dev(S, "S", torch.float64, N * N), _stream_ptr(stream))
     if st != OK:
         raise PouError(st, "pou_gram_noalloc")
 
@@ -377,18 +397,23 @@ def gram_workspace_bytes(dtype_code, ng, N):
 
 
 def cholinv(S, Rinv, info, stream=None):
-    st = _lib.pou_cholinv(S.shape[0], C.c_void_p(S.data_ptr()), C.c_void_p(Rinv.data_ptr()),
-                          C.c_void_p(info.data_ptr()), _stream_ptr(stream))
+    import torch
+    N = S.shape[0]
+    st = _lib.pou_cholinv(N, _dev(S, "S", torch.float64, N * N), _dev(Rinv, "Rinv", torch.float64, N * N),
+                          _dev(info, "info", torch.int32, 1), _stream_ptr(stream))
     if st != OK:
         raise PouError(st, "pou_cholinv")
 
 
 def rotate(A, Rinv, B, rho=None, stream=None):
+    import torch
+    _dev(A, "A")
     N = A.shape[0]
     ng = A.numel() // N
     p, dt, _ = _ptr(A)
-    st = _lib.pou_rotate(dt, ng, N, p, C.c_void_p(Rinv.data_ptr()), C.c_void_p(B.data_ptr()),
-                         C.c_void_p(rho.data_ptr()) if rho is not None else None, _stream_ptr(stream))
+    bp = _dev(B, "B", A.dtype, A.numel())
+    rp = _dev(rho, "rho", torch.float64, ng) if rho is not None else None
+    st = _lib.pou_rotate(dt, ng, N, p, _dev(Rinv, "Rinv", torch.float64, N * N), bp, rp, _stream_ptr(stream))
     if st != OK:
         raise PouError(st, "pou_rotate")
 
@@ -399,10 +424,12 @@ def hartree_workspace_bytes(n):
 
 
 def hartree(n, L, rho, vh, workspace, stream=None):
+    import torch
     narr = (C.c_int * 3)(*n)
     Larr = (C.c_double * 3)(*L)
-    st = _lib.pou_hartree(narr, Larr, C.c_void_p(rho.data_ptr()), C.c_void_p(vh.data_ptr()),
-                          C.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size(),
+    ng = int(n[0]) * int(n[1]) * int(n[2])
+    st = _lib.pou_hartree(narr, Larr, _dev(rho, "rho", torch.float64, ng), _dev(vh, "vh", torch.float64, ng),
+                          _dev(workspace, "workspace"), workspace.numel() * workspace.element_size(),
                           _stream_ptr(stream))
     if st != OK:
         raise PouError(st, "pou_hartree")

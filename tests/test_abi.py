@@ -77,3 +77,22 @@ def test_product_path_does_not_import_the_oracle():
             "print(any(m == 'oracle' or m.startswith('oracle.') for m in sys.modules))")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT)
     assert r.stdout.strip() == "False", r.stderr
+
+
+def test_standalone_ops_refuse_host_tensors(pou):
+    """The stand-alone operations take device memory: host tensors are refused
+    before the library is called (and the library refuses host pointers)."""
+    torch = pytest.importorskip("torch")
+    A = torch.zeros((4, 64), dtype=torch.float32)
+    S = torch.zeros((4, 4), dtype=torch.float64)
+    with pytest.raises(ValueError):
+        pou.gram(A, 1.0, S, torch.zeros(1024, dtype=torch.float64))
+    with pytest.raises(ValueError):
+        pou.gram_noalloc(A, 1.0, S)
+    with pytest.raises(ValueError):
+        pou.cholinv(S, torch.zeros_like(S), torch.zeros(1, dtype=torch.int32))
+    with pytest.raises(ValueError):
+        pou.rotate(A, S, torch.zeros_like(A))
+    with pytest.raises(ValueError):
+        pou.hartree((4, 4, 4), (1.0, 1.0, 1.0), torch.zeros(64, dtype=torch.float64),
+                    torch.zeros(64, dtype=torch.float64), torch.zeros(4096, dtype=torch.float64))
