@@ -299,6 +299,9 @@ class Solver:
             gp, gdt, gdev = _ptr(dEdU)
             if U is None:
                 dt, dev = gdt, gdev
+            elif (gdt, gdev) != (dt, dev):
+                # one dtype and one on_device flag describe both arrays in the call
+                raise TypeError("dEdU must have the dtype and the device of U")
         dR = np.zeros((self.M, 3)) if atoms else None
         dZ = np.zeros(self.M) if atoms else None
         self._check(_lib.pou_backward(self._ctx, p, dt, dev, float(g), gp,

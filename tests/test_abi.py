@@ -4,6 +4,7 @@ import os
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -96,3 +97,13 @@ def test_standalone_ops_refuse_host_tensors(pou):
     with pytest.raises(ValueError):
         pou.hartree((4, 4, 4), (1.0, 1.0, 1.0), torch.zeros(64, dtype=torch.float64),
                     torch.zeros(64, dtype=torch.float64), torch.zeros(4096, dtype=torch.float64))
+
+
+def test_backward_refuses_mismatched_output(pou):
+    """U and dE/dU share one dtype code and one on_device flag in the call:
+    the binding refuses an output of another dtype before the library runs."""
+    s = pou.Solver.__new__(pou.Solver)  # no context: the check comes first
+    s.M = 0
+    s._ctx = None
+    with pytest.raises(TypeError):
+        pou.Solver.backward(s, np.zeros((2, 8)), 1.0, np.zeros((2, 8), dtype=np.float32))

@@ -292,6 +292,32 @@ def test_large_n_fp64_form_is_einval(P):
         solver(P, (16, 16, 18), (6.0, 6.0, 7.0), 192, precision=1, n_diag=50)
 
 
+def test_full_size_160_energy_and_h_apply(P):
+    """The bench's workload at full size (160^3 grid, N = 128, 13-point
+    stencil, mixed form): the energy terms of an orthonormal block and
+    H(rho) W on sampled orbitals (through the adjoint, dE/dU = 2 f dV H U)
+    against the oracle.  The oracle orthonormalises the seeded start in FP64;
+    both sides then work on the same FP32-rounded block."""
+    w, R, Z, U0 = inputs.workload_inputs("l30_g160_n128")
+    cfg = ocfg(w.n, w.L, w.N, order=w.order)
+    W, _, _ = O.cholesky_qr(U0, cfg)
+    del U0
+    W = np.ascontiguousarray(W.astype(np.float32).astype(np.float64))
+    vext = O.vext_gaussians(cfg, R, Z, w.width)
+    s = solver(P, w.n, w.L, w.N, order=w.order, precision=1)
+    s.set_atoms(R, Z, w.width)
+    got = s.evaluate(W)
+    ref = O.energy_terms(W, vext, cfg)
+    for k in ("kinetic", "external", "hartree", "exchange"):
+        assert abs(got[k] - getattr(ref, k)) <= 2e-6 * max(1.0, abs(getattr(ref, k))), k
+    out = np.empty(W.shape)
+    s.backward(W, 1.0 / (2 * O.F_OCC * cfg.dV), out)
+    idx = [0, 77, 127]
+    ref_h = O.apply_h(W[idx], O.total_potential(O.density(W), vext, cfg), cfg)
+    np.testing.assert_allclose(out[idx].astype(np.float64), ref_h, atol=2e-5 * np.max(np.abs(ref_h)))
+    s.close()
+
+
 def test_full_size_512_orbitals(P):
     """The 192^3 grid with N = 512 (14.5 GB per FP32 block), in the launch
     configuration the bench times: properties that hold at any size, checked
