@@ -117,7 +117,7 @@ typedef struct {
   int forced;            /* trials accepted after max_backtrack reductions */
   int total_iterations;  /* accepted steps since pou_set_orbitals */
   int converged;         /* 0: no, 1: energy criterion met, 2: gradient criterion met */
-  double energy;         /* E of the current orbitals, Ha */
+  double energy;         /* E of the current orbitals, Ha (n_org > 1: of the last orthonormalised step) */
   double tau;            /* last accepted step */
   double df_mean3;       /* (df^l + df^(l-1) + df^(l-2)) / 3 of Sec. 4.2 */
   double grad_norm;      /* ||HW - W Sigma||_F (Eq. gra) when computed, else -1 */
@@ -156,14 +156,16 @@ pou_status pou_set_atoms(pou_ctx* ctx, int M, const double* R, const double* Z, 
  * in dtype.  ENOTSPD if U is rank deficient. */
 pou_status pou_set_orbitals(pou_ctx* ctx, const void* U, int dtype, int on_device);
 
-/* Run up to max_iter accepted steps of Algorithm E.  Stops early when
+/* Run up to max_iter accepted steps of Algorithm E (Algorithm M with the
+ * config's n_org and n_diag, Sec. 3.3).  Stops early when
  * e_tol > 0 and the mean of the last three relative energy changes is below
  * e_tol (Sec. 4.2), or when grad_tol > 0 and ||grad E||_F < grad_tol
  * (Eq. gra; checked every 10 steps).  rep may be NULL.  Returns ENOCONV if a
  * tolerance was given and not met, ENOTSPD / ENAN on breakdown. */
 pou_status pou_iterate(pou_ctx* ctx, int max_iter, double e_tol, double grad_tol, pou_report* rep);
 
-/* Energy terms of the current orbitals (FP64). */
+/* Energy terms of the current orbitals (FP64); with n_org > 1, those of the
+ * last orthonormalised step (the steps in between are not orthonormal). */
 pou_status pou_energy(pou_ctx* ctx, pou_energy_terms* out);
 
 /* Copy out the current orbitals, converted to dtype. */
@@ -199,8 +201,9 @@ pou_status pou_backward(pou_ctx* ctx, const void* U, int dtype, int on_device, d
                         void* dEdU, double* dEdR, double* dEdZ);
 
 /* Per-iteration history since pou_set_orbitals (Fig. 3 style curves):
- * up to max_entries accepted energies and steps, oldest first; *count gets the
- * number written.  E, tau may be NULL. */
+ * up to max_entries accepted energies and steps, oldest first (NaN energy
+ * for the steps between orthonormalisations when n_org > 1); *count gets
+ * the number written.  E, tau may be NULL. */
 pou_status pou_get_history(pou_ctx* ctx, double* E, double* tau, int max_entries, int* count);
 
 /* Checkpoint / resume: the scalar history (tau, C, Q, sigma, step counters)
