@@ -425,6 +425,20 @@ def test_algorithm_m_n_org_same_minimum_and_structure(n_org):
             assert np.max(np.abs(O.inner_matrix(st.W, st.W, cfgm) - np.eye(4))) < 1e-12
 
 
+def test_trial_gram_is_near_identity():
+    """Fig. 2: the Gram matrix <Wt^T Wt> of the trial point stays close to the
+    identity, and so diagonally dominant, away from the first steps; the
+    exceptions are single large Barzilai-Borwein steps."""
+    w, R, Z, U0 = inputs.workload_inputs("l10_g32_n4")
+    cfg = O.cubic(w.n, w.L, order=w.order, N=w.N)
+    vext = O.vext_gaussians(cfg, R, Z, w.width)
+    st = O.run(U0, vext, cfg, 300)
+    g = np.array([h.gram_offdiag for h in st.history])[100:]
+    assert np.median(g) < 1e-3
+    assert np.percentile(g, 90) < 1e-2
+    assert np.mean(g < 1.0 / w.N) > 0.95  # max |S - I| < 1/N: S diagonally dominant
+
+
 @pytest.mark.slow
 def test_bb_trajectory_is_chaotic():
     """A 1e-15 relative change of U0 moves the oracle's energy by > 1e-8 within 200 steps
