@@ -107,3 +107,36 @@ def test_backward_refuses_mismatched_output(pou):
     s._ctx = None
     with pytest.raises(TypeError):
         pou.Solver.backward(s, np.zeros((2, 8)), 1.0, np.zeros((2, 8), dtype=np.float32))
+
+
+def test_every_boundary_function_is_documented():
+    """Each function of the C-ABI header has a comment block right above its
+    declaration (what it computes, with its section or equation, arguments,
+    layout, ownership and errors)."""
+    import re
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "pou.h")).read()
+    lines = hdr.splitlines()
+    missing = []
+    for i, ln in enumerate(lines):
+        m = re.match(r"^(?:pou_status|void|const char\*|size_t|long long)\s+(pou_\w+)\(", ln)
+        if not m:
+            continue
+        # declarations written together (no blank line between them) share
+        # one comment; a blank line ends the group
+        j = i - 1
+        while j >= 0 and lines[j].strip() and not lines[j].rstrip().endswith("*/"):
+            j -= 1
+        if j < 0 or not lines[j].strip():
+            missing.append(m.group(1))
+    assert not missing, missing
+
+
+def test_product_package_does_not_import_the_oracle():
+    """The oracle is test infrastructure: nothing in the library package
+    imports it (no CPU fallback through it)."""
+    pkg = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1510_07230_gb300")
+    for root, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(root, f)).read()
+                assert "pou_oracle" not in text and "import oracle" not in text and "from oracle" not in text, f
