@@ -453,3 +453,113 @@ def test_bb_trajectory_is_chaotic():
     d = np.abs(np.array([h.energy for h in a.history]) - np.array([h.energy for h in b.history]))
     assert np.max(d[:80]) < 1e-10
     assert np.max(d) > 1e-8
+
+
+def test_subspace_rotation_diagonalises_sigma():
+    """Sec. 3.3 subspace diagonalisation, checked on what it must produce
+    rather than on E (every orthogonal rotation leaves E unchanged): after
+    W <- W P, Sigma = <W^T H W> is diagonal, its diagonal ascends and carries
+    the spectrum of the Sigma before the rotation (same trace, same sum of
+    squares, same ordered eigenvalues), the span and rho are unchanged, and
+    W stays orthonormal.  A transposed P leaves P Sigma P^T, which is not
+    diagonal; unsorted eigenpairs fail the ordering."""
+    cfg = O.cubic(10, 7.0, order=4, N=5)
+    R, Z = inputs.atoms(51, 3, 7.0, "const4")
+    vext = O.vext_gaussians(cfg, R, Z, 0.8)
+    st = O.run(inputs.random_orbitals(51, 5, cfg.n), vext, cfg, 25)
+    W0, rho0, E0 = st.W.copy(), st.rho.copy(), st.E
+    H0 = O.apply_h(W0, st.V, cfg)
+    Sig0 = cfg.dV * (W0.reshape(5, -1) @ H0.reshape(5, -1).T)
+    off0 = np.max(np.abs(Sig0 - np.diag(np.diag(Sig0))))
+    assert off0 > 1e-3  # far from diagonal before: the check below is not vacuous
+    O.subspace_diagonalise(st, vext, cfg)
+    W1 = st.W
+    H1 = O.apply_h(W1, st.V, cfg)
+    Sig1 = cfg.dV * (W1.reshape(5, -1) @ H1.reshape(5, -1).T)
+    d = np.diag(Sig1)
+    scale = np.max(np.abs(Sig0))
+    assert np.max(np.abs(Sig1 - np.diag(d))) < 1e-12 * scale
+    assert np.all(np.diff(d) > 0)
+    # invariants of an orthogonal similarity: trace and Frobenius norm
+    assert abs(d.sum() - np.trace(Sig0)) < 1e-12 * scale
+    assert abs(np.sum(d * d) - np.sum((0.5 * (Sig0 + Sig0.T)) ** 2)) < 1e-11 * scale ** 2
+    # the ordered eigenvalues of the symmetric 5 x 5 matrix, from its characteristic polynomial
+    lam = np.sort(np.roots(np.poly(0.5 * (Sig0 + Sig0.T))).real)
+    np.testing.assert_allclose(d, lam, atol=1e-9 * scale)
+    # span, orthonormality, density and energy unchanged
+    M = cfg.dV * (W0.reshape(5, -1) @ W1.reshape(5, -1).T)
+    assert abs(np.sum(M * M) - 5.0) < 1e-12
+    assert np.max(np.abs(O.inner_matrix(W1, W1, cfg) - np.eye(5))) < 1e-12
+    np.testing.assert_allclose(O.density(W1), rho0, atol=1e-12 * np.max(rho0))
+    assert abs(O.energy(W1, vext, cfg) - E0) < 1e-11
+    # the step after the rotation uses the Barzilai-Borwein step of the pair
+    # before it (traces are invariant under the rotation of both iterates)
+    assert st.tau_next is not None and st.W_prev is None
+
+
+def test_nonmonotone_reference_closed_form():
+    """Eq. (ene-de): Q^(l+1) = eta Q^l + 1, C^(l+1) = (eta Q^l C^l + E^(l+1)) / Q^(l+1)
+    with C^0 = E^0, Q^0 = 1.  Unrolling, Q^l C^l = sum_k eta^(l-k) E^k and
+    Q^l = sum_k eta^(l-k), so C^l is the eta-weighted mean of E^0..E^l.  The
+    oracle's C and Q along an eta = 0.85 trajectory must equal that closed
+    form, and every accepted (not forced) step must satisfy the test with C
+    taken from it."""
+    eta = 0.85
+    cfg = O.cubic(10, 7.0, order=2, N=4, eta=eta)
+    R, Z = inputs.atoms(33, 2, 7.0, "const4")
+    vext = O.vext_gaussians(cfg, R, Z, 0.8)
+    st = O.initial_state(inputs.random_orbitals(33, 4, cfg.n), vext, cfg)
+    E = [st.E]
+    C_seen, Q_seen = [st.C], [st.Q]
+    backtracked = 0
+    for _ in range(30):
+        O.iterate(st, vext, cfg)
+        E.append(st.history[-1].energy)
+        C_seen.append(st.C)
+        Q_seen.append(st.Q)
+        backtracked += st.history[-1].backtracks
+    E = np.array(E)
+    for l in range(len(E)):
+        wts = eta ** np.arange(l, -1, -1, dtype=float)  # eta^(l-k), k = 0..l
+        Cl = float(np.dot(wts, E[: l + 1]) / wts.sum())
+        assert abs(C_seen[l] - Cl) < 1e-12 * abs(Cl)
+        assert abs(Q_seen[l] - wts.sum()) < 1e-13 * wts.sum()
+        if l > 0:
+            rec = st.history[l - 1]
+            wp = eta ** np.arange(l - 1, -1, -1, dtype=float)
+            Cprev = float(np.dot(wp, E[:l]) / wp.sum())
+            if not rec.forced:
+                assert E[l] <= Cprev - cfg.rho1 * rec.tau * rec.znorm2 + 1e-12
+    # C is a weighted mean, not the last energy: it lags above E on a descending run
+    assert np.sum(np.array(C_seen[1:]) > E[1:] + 1e-9) > 10
+
+
+def test_converged_forces_match_fd_of_reconverged_energies():
+    """Sec. 2.1: at the minimum over orthonormal U the derivative of the
+    converged energy E*(R) equals the explicit dE/dR at fixed U (the U-gradient
+    H u_i lies in the span, so the orbitals' response does not enter).  The
+    analytic gradient of the converged orbitals must match central differences
+    of energies re-converged at R +- 1e-4 bohr, to 1e-5 Ha/bohr."""
+    cfg = O.cubic(8, 6.0, order=2, N=2)
+    R = np.array([[1.3, 2.1, 2.6], [3.9, 3.4, 4.2]])
+    Zc = np.array([3.0, 2.0])
+    U0 = inputs.random_orbitals(61, 2, cfg.n)
+
+    def converge(Rv, U):
+        vext = O.vext_gaussians(cfg, Rv, Zc, 0.8)
+        st = O.run(U, vext, cfg, 4000, e_tol=1e-16)
+        return st
+
+    st = converge(R, U0)
+    dR, _ = O.energy_gradient_atoms(st.W, cfg, R, Zc, 0.8)
+    assert np.max(np.abs(dR)) > 1e-2  # the atoms feel a real force
+    h = 1e-4
+    for I in range(2):
+        for a in range(3):
+            Rp, Rm = R.copy(), R.copy()
+            Rp[I, a] += h
+            Rm[I, a] -= h
+            Ep = converge(Rp, st.W).E
+            Em = converge(Rm, st.W).E
+            fd = (Ep - Em) / (2 * h)
+            assert abs(fd - dR[I, a]) < 1e-5, (I, a, fd, dR[I, a])
