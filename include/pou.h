@@ -249,17 +249,20 @@ pou_status pou_gram(int dtype, long long Ng, int N, const void* A, double dV, do
                     void* workspace, size_t workspace_bytes, void* stream);
 
 /* Allocation-free Gram matrix: the result of pou_gram (same arguments
- * without the workspace), for callers that cannot allocate device memory,
- * for example code that runs while a stream is captured into a CUDA graph
- * (cudaMalloc is not a stream operation and synchronises the device), loops
- * that must not allocate after start-up, or hosts that give this library a
- * fixed memory budget.  The paper has no counterpart: this is a library
+ * without the workspace), for callers that cannot allocate device memory:
+ * hosts that give this library a fixed device-memory budget, and loops that
+ * must not call cudaMalloc once they run (it can synchronise the device and
+ * stall every stream).  The paper has no counterpart: this is a library
  * service, not a step of the method.
  *  - The per-split partial sums live in one fixed buffer of static device
  *    memory of POU_GRAM_NOALLOC_MAX_BYTES, which every GPU that loads the
  *    library holds until the process exits; the call allocates nothing.
  *  - The first call on a device looks up the buffer's device address, with
- *    that device current; make that first call before any stream capture.
+ *    that device current, and keeps it for the life of the process; make
+ *    that first call before any stream capture.  The kept address assumes
+ *    the device's primary context: after cudaDeviceReset, or from another
+ *    driver context on the same device, the buffer moves and the kept
+ *    address is stale.
  *  - The number of splits is capped to what fits the buffer, so results may
  *    differ from pou_gram by rounding; N > POU_MAX_N (or a split that does
  *    not fit) returns POU_EINVAL.

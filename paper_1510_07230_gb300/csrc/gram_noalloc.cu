@@ -1,13 +1,14 @@
 // Allocation-free Gram matrix: the entry point pou_gram_noalloc of pou.h.
 //
 // pou_gram needs a caller-provided device workspace for the per-split FP64
-// partial sums.  Some callers cannot provide one: code that runs while a
-// stream is being captured into a CUDA graph (cudaMalloc is not a stream
-// operation and synchronises the device), real-time loops that must not
-// allocate after start-up, and hosts that hand this library a fixed device
-// memory budget.  This variant keeps the partial sums in a fixed buffer of
-// static device memory instead, which every GPU that loads the library
-// holds until the process exits.
+// partial sums.  Some callers cannot provide one: hosts that hand this
+// library a fixed device-memory budget, and loops that must not call
+// cudaMalloc once they run (it can synchronise the device and stall every
+// stream).  This variant keeps the partial sums in a fixed buffer of static
+// device memory instead, which every GPU that loads the library holds until
+// the process exits.  The buffer's device address is looked up once per
+// device and kept; that assumes the device's primary context (no
+// cudaDeviceReset, no other driver context on the device).
 #include "pou.h"
 #include "pou_internal.cuh"
 

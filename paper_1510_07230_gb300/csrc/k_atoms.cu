@@ -142,7 +142,7 @@ void launch_atom_tables(const double* R, const double* Z, int M, double width, c
 
 void launch_vext(const double* Z, int M, const int n[3], const AtomTables& t, double* vext, cudaStream_t s) {
   prof_begin("vext", s);
-  k_vext<<<152 * 8, 256, 0, s>>>(Z, M, n[0], n[1], n[2], t, vext);
+  k_vext<<<num_sms() * 8, 256, 0, s>>>(Z, M, n[0], n[1], n[2], t, vext);
   prof_end(s);
 }
 

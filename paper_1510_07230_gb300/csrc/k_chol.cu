@@ -516,7 +516,7 @@ void launch_cholinv_big(const State* st, const double* S, double* Rinv, int N, i
   }
   k_big_invdiag<<<np, 32, 0, s>>>(a);
   for (int d = 1; d < np; ++d) k_big_invlevel<<<np - d, 256, 0, s>>>(a, d);
-  k_big_final<<<std::max(1, std::min(152, (N * (N - 1) / 2 + 255) / 256)), 256, 0, s>>>(a, info);
+  k_big_final<<<std::max(1, std::min(num_sms(), (N * (N - 1) / 2 + 255) / 256)), 256, 0, s>>>(a, info);
 }
 }  // namespace
 

@@ -497,7 +497,7 @@ int launch_potential(const FftPlan& p, const PotArgs<T>& pa, cudaStream_t s) {
     a.dv32 = reinterpret_cast<float*>(pa.dv_out);
   }
   if (!pa.hartree && !pa.vh_out) {
-    const int nblk = 152 * 4;
+    const int nblk = num_sms() * 4;
     prof_begin("potential_local", s);
     k_potential_local<T><<<nblk, FNT, 0, s>>>(a, ng);
     prof_end(s);

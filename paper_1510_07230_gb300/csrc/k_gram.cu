@@ -653,7 +653,7 @@ __global__ void k_scale_copy(const T* in, T* out, T scale, i64 n) {
 
 int grid_for(i64 n) {
   i64 b = (n + 255) / 256;
-  if (b > 152 * 16) b = 152 * 16;
+  if (b > num_sms() * 16) b = num_sms() * 16;
   if (b < 1) b = 1;
   return (int)b;
 }
@@ -674,7 +674,7 @@ void gram_layout(i64 ng, int N, bool general, int* nsplit, int* npair, i64* chun
   const int np = general ? nsup * nsup : nsup * (nsup + 1) / 2;
   const i64 ntiles = (ng + BK - 1) / BK;
   // one CTA per SM in total (one wave), at least 32 tiles per CTA
-  i64 g = std::max(1, 152 / np);
+  i64 g = std::max(1, num_sms() / np);
   g = std::max<i64>(1, std::min<i64>(g, ntiles / 32));
   *npair = np;
   *chunk = ntiles;  // tiles over the whole grid
@@ -779,7 +779,7 @@ template int launch_residual<double>(const double*, const double*, const double*
 int rotate_grid(i64 ng, int elem_bytes) {
   if (elem_bytes == 4) return rotate_tc_grid(ng);
   const int nchunks = (int)((ng + RP - 1) / RP);
-  return std::min(nchunks, 152);
+  return std::min(nchunks, num_sms());
 }
 
 template <typename T>
@@ -790,7 +790,7 @@ void launch_rotate(const RotArgs<T>& a, cudaStream_t s) {
       // tensor-core rotation takes upper triangular R^-1 only)
       const int nchunks = (int)((a.ng + RP - 1) / RP);
       prof_begin(rotate_prof_name(a.trial, a.src_trial_slot, a.src_cur_slot), s);
-      k_rotate_f32_cc<<<std::min(nchunks, 2 * 152), RNT, rotate_f32_smem(), s>>>(a, nchunks);
+      k_rotate_f32_cc<<<std::min(nchunks, 2 * num_sms()), RNT, rotate_f32_smem(), s>>>(a, nchunks);
       prof_end(s);
     } else {
       launch_rotate_tc(a, s);

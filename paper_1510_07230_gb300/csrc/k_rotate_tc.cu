@@ -869,7 +869,7 @@ bool g_configured = false;
 
 int rotate_tc_grid(i64 ng) {
   const i64 ntiles = (ng + TPTS - 1) / TPTS;
-  return (int)std::max<i64>(1, std::min<i64>(152, ntiles));
+  return (int)std::max<i64>(1, std::min<i64>(num_sms(), ntiles));
 }
 
 void configure_rotate_tc() {

@@ -26,6 +26,25 @@ namespace pou {
 long long g_launches = 0;
 thread_local ProfRecorder* g_prof = nullptr;
 
+int num_sms() {
+  constexpr int kMaxDev = 64;
+  static int cache[kMaxDev] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+    cudaGetLastError();
+    return 152;  // GB300; the launch that follows reports the device error
+  }
+  if (cache[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+      cudaGetLastError();
+      v = 152;
+    }
+    cache[dev] = v;
+  }
+  return cache[dev];
+}
+
 namespace {
 
 constexpr int TX = 32;
@@ -606,7 +625,7 @@ int apply_h_ntile(int nx, int ny, int nz, int N, int* nzc_out) {
   const long long base = (long long)ntx * nty * N;
   int nzc = 1;
   // enough CTAs to fill the GPU several times, with z sweeps of >= 8 planes
-  while (base * nzc < 4 * 152 * 8 && nz / (nzc * 2) >= 8) nzc *= 2;
+  while (base * nzc < 4LL * num_sms() * 8 && nz / (nzc * 2) >= 8) nzc *= 2;
   if (nzc_out) *nzc_out = nzc;
   return ntx * nty * nzc;
 }

@@ -915,7 +915,7 @@ static pou_status create_buffers(pou_ctx* c) {
   DALLOC(c->work, c->ng * sizeof(double2));
   c->ntile = apply_h_ntile(c->nx, c->ny, c->nz, c->N, nullptr);
   DALLOC(c->tilepart, (size_t)c->N * c->ntile * NPT * sizeof(double));
-  c->neblk_max = (int)std::max<long long>(152 * 4, (long long)c->nz * c->ny);
+  c->neblk_max = (int)std::max<long long>((long long)num_sms() * 4, (long long)c->nz * c->ny);
   DALLOC(c->epart, (size_t)c->neblk_max * NE * sizeof(double));
   DALLOC(c->S, (size_t)c->N * c->N * sizeof(double));
   DALLOC(c->Rinv, (size_t)c->N * c->N * sizeof(double));

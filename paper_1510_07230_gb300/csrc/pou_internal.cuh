@@ -286,6 +286,10 @@ inline const char* rotate_prof_name(int trial, int src_trial_slot, int src_cur_s
                                                                                     : "rotate_plain";
 }
 
+// Streaming multiprocessors of the current device, queried once per device;
+// launch shapes are sized in multiples of it.
+int num_sms();
+
 // Counts every kernel launched by the library (host side).
 extern long long g_launches;
 

@@ -318,6 +318,70 @@ def test_full_size_160_energy_and_h_apply(P):
     s.close()
 
 
+def test_bench_kernel_configuration_mixed_n128_13pt(P):
+    """The launch configuration the bench times (mixed form, N = 128, 13-point
+    stencil: the tensor-core trial Gram over one 128 x 128 block, the
+    tensor-core rotation with all four 32-orbital atoms of R^-1, the one-CTA
+    Cholesky) on a 40^3 grid the oracle steps through in seconds.  The first
+    steps follow the FP64 oracle's trajectory from the same FP32-rounded
+    start; at least one of them takes the second Cholesky-QR pass; the
+    returned orbitals are orthonormal, and the energy, density and residual
+    norm the library reports are those the oracle computes from them."""
+    n, L, N = 40, 16.0, 128
+    R, Z = inputs.atoms(71, 32, L, "uniform26")
+    U = inputs.random_orbitals(71, N, (n, n, n)).astype(np.float32)
+    cfg = ocfg(n, L, N, order=4)
+    vext = O.vext_gaussians(cfg, R, Z, 0.8)
+    s = solver(P, n, L, N, order=4, precision=1)
+    s.set_atoms(R, Z, 0.8)
+    s.set_orbitals(U)
+    steps = 8
+    rep = s.iterate(steps)
+    assert rep["iterations"] == steps
+    assert rep["second_passes"] >= 1
+    Eg, _ = s.history()
+    st = O.run(U.astype(np.float64), vext, cfg, steps)
+    Eo = np.array([h.energy for h in st.history])
+    np.testing.assert_allclose(Eg[:steps], Eo[:steps], rtol=2e-6)
+    W = s.get_orbitals().astype(np.float64)
+    assert np.max(np.abs(O.inner_matrix(W, W, cfg) - np.eye(N))) < 2e-6
+    e = s.energy()
+    ref = O.energy_terms(W, vext, cfg)
+    assert abs(ref.total - e["total"]) <= 1e-7 * abs(ref.total)
+    for k in ("kinetic", "external", "hartree", "exchange"):
+        assert abs(e[k] - getattr(ref, k)) <= 2e-7 * max(1.0, abs(getattr(ref, k))), k
+    np.testing.assert_allclose(s.get_density(), O.density(W), rtol=1e-6, atol=1e-9)
+    HW = O.apply_h(W, O.total_potential(O.density(W), vext, cfg), cfg)
+    g_ref = O.gradient_residual(W, HW, cfg)
+    assert abs(s.gradient_norm() - g_ref) <= 3e-3 * g_ref + 2e-5
+    s.close()
+
+
+def test_full_size_160_reported_energy_after_200_steps(P):
+    """The bench's workload (160^3, N = 128, 13-point, mixed form) after the
+    200 steps the bench takes before timing: the energy the library reports
+    is the oracle's energy of the orbitals it returns, which are orthonormal
+    (checked on a sample of 16 orbitals against the whole block)."""
+    w, R, Z, U0 = inputs.workload_inputs("l30_g160_n128")
+    cfg = ocfg(w.n, w.L, w.N, order=w.order)
+    vext = O.vext_gaussians(cfg, R, Z, w.width)
+    s = solver(P, w.n, w.L, w.N, order=w.order, precision=1)
+    s.set_atoms(R, Z, w.width)
+    s.set_orbitals(U0)
+    del U0
+    rep = s.iterate(200)
+    assert rep["iterations"] == 200
+    W = s.get_orbitals().astype(np.float64)
+    e = s.energy()["total"]
+    s.close()
+    idx = np.arange(0, w.N, 8)
+    G = cfg.dV * (W[idx].reshape(len(idx), -1) @ W.reshape(w.N, -1).T)
+    G[np.arange(len(idx)), idx] -= 1.0
+    assert np.max(np.abs(G)) < 2e-6
+    ref = O.energy(W, vext, cfg)
+    assert abs(ref - e) <= 1e-6 * abs(ref), (ref, e)
+
+
 def test_full_size_512_orbitals(P):
     """The 192^3 grid with N = 512 (14.5 GB per FP32 block), in the launch
     configuration the bench times: properties that hold at any size, checked
