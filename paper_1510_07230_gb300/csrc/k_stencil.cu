@@ -588,6 +588,310 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_apply_h_pair(App
   }
 }
 
+// ----------------------------------------------------------------------------
+// FP32 form with even nx.  Each thread owns two adjacent x points (one
+// float2 per array).  Differences from the paired kernel above, each removing
+// per-point work:
+//   * the step s = w - w' is formed once per cell when its plane arrives (each
+//     thread converts the cells it copied itself, before the barrier), so the
+//     s-stencil reads s directly; the (V - V') w' term is formed there too and
+//     stored in the V - V' slot;
+//   * the z-neighbours live in circular register queues of the ring's length,
+//     indexed at compile time (the plane loop is unrolled by the ring size),
+//     so the queues are never shifted;
+//   * on cubic grids the three per-axis kinetic sums are one sum of
+//     w (e_x + e_y + e_z) (the FP64 coefficients are then equal);
+//   * the tile is 32 points x 16 rows, so grids of 32k points in x tile
+//     exactly.
+namespace pk {
+
+constexpr int TXP = 16;         // threads per tile row
+constexpr int TYP = 16;         // tile rows
+constexpr int NTP = TXP * TYP;  // threads per CTA
+constexpr int PW = 2 * TXP;     // points per tile row
+constexpr int ROW = PW + 4;     // shared row: two halo cells each side
+constexpr int PFP = 2;          // planes in flight
+
+template <int R, bool HIST>
+struct Stage {
+  float w[TYP + 2 * R][ROW];
+  float s[HIST ? TYP + 2 * R : 1][ROW];  // w' on arrival, then s = w - w'
+  float v[TYP][PW];
+  float dv[HIST ? TYP : 1][PW];          // V - V' on arrival, then (V - V') w'
+};
+
+// Per-lane FP32 arithmetic on the pair, each lane rounded as one scalar
+// operation (no contraction across helpers).  Measured against the packed
+// f32x2 instructions of sm_100+ in the same kernel: equal time and bit-equal
+// results, while this form needs fewer registers (80 on cubic grids: three
+// CTAs per SM).
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+  return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y));
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  return make_float2(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y));
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  return make_float2(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y));
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  return make_float2(__fmaf_rn(a.x, b.x, c.x), __fmaf_rn(a.y, b.y, c.y));
+}
+__device__ __forceinline__ float2 splat(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 lds2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+__device__ __forceinline__ void sts2(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
+
+// Compensated (Kahan) sum per lane, with the compensation kept negated so
+// that the product enters through one FMA: y = a b - c, t = s + y,
+// c = (t - s) - y.
+struct K2 {
+  float2 s, nc;
+  __device__ __forceinline__ void add_prod(float2 a, float2 b) {
+    const float2 y = fma2(a, b, nc);
+    const float2 t = add2(s, y);
+    nc = add2(sub2(s, t), y);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const {
+    return ((double)s.x + (double)nc.x) + ((double)s.y + (double)nc.y);
+  }
+};
+
+// Second differences of one array at the pair (no 1/h^2), for order R:
+// (u[+d] - u) + (u[-d] - u); order 4 combines 16 d1 - d2.  xm2/xp2 are the
+// pairs (x-2, x-1) and (x+2, x+3) of the shared row.
+template <int R>
+__device__ __forceinline__ void second_diffs(float2 c, float2 xm2, float2 xp2, float2 ym1, float2 yp1, float2 ym2,
+                                             float2 yp2, float2 zm1, float2 zp1, float2 zm2, float2 zp2, float2& ex,
+                                             float2& ey, float2& ez) {
+  const float2 xm1 = make_float2(xm2.y, c.x), xp1 = make_float2(c.y, xp2.x);
+  const float2 dx1 = add2(sub2(xp1, c), sub2(xm1, c));
+  const float2 dy1 = add2(sub2(yp1, c), sub2(ym1, c));
+  const float2 dz1 = add2(sub2(zp1, c), sub2(zm1, c));
+  if (R == 1) {
+    ex = dx1;
+    ey = dy1;
+    ez = dz1;
+  } else {
+    const float2 s16 = splat(16.f);
+    // -(d2) formed directly, so that 16 d1 - d2 is one FMA
+    const float2 ndx2 = add2(sub2(c, xp2), sub2(c, xm2));
+    const float2 ndy2 = add2(sub2(c, yp2), sub2(c, ym2));
+    const float2 ndz2 = add2(sub2(c, zp2), sub2(c, zm2));
+    ex = fma2(s16, dx1, ndx2);
+    ey = fma2(s16, dy1, ndy2);
+    ez = fma2(s16, dz1, ndz2);
+  }
+}
+
+template <int R, bool HIST, bool CUBIC>
+__global__ void __launch_bounds__(NTP, CUBIC ? 3 : 2) k_apply_h_pk(ApplyArgs<float> a) {
+  constexpr int S = R + 2 + PFP;  // ring of planes; also the length of the register queues
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Stage<R, HIST>* ring = reinterpret_cast<Stage<R, HIST>*>(smem_raw);
+  __shared__ double red[NTP / 32][NPT];
+
+  if (a.st && a.st->done) return;
+  if (a.mode == 3 && !a.st->diag_now) return;
+  const int cur = a.st ? a.st->cur : 0;
+  const int t = (a.mode == 2) ? 0 : (a.mode == 3 ? cur : 1 - cur);
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const i64 pl = (i64)nx * ny;
+  const i64 ng = pl * nz;
+  const int orb = blockIdx.z;
+  const float* w = a.W[t] + (i64)orb * ng;
+  float* hw = a.HW[t] ? a.HW[t] + (i64)orb * ng : nullptr;
+  const float* V = a.V[t];
+  const float* wp = HIST ? a.W[cur] + (i64)orb * ng : nullptr;
+  const float* dVp = HIST ? a.dV : nullptr;
+  const float sigp = (HIST || a.mode == 3) ? (float)a.sigma[cur][orb] : 0.f;
+
+  const int ntx = (nx + PW - 1) / PW;
+  const int tx0 = (blockIdx.x % ntx) * PW;
+  const int ty0 = (blockIdx.x / ntx) * TYP;
+  const int z0 = (int)(((i64)blockIdx.y * nz) / a.nzc);
+  const int z1 = (int)(((i64)(blockIdx.y + 1) * nz) / a.nzc);
+  const int lx = threadIdx.x, ly = threadIdx.y;
+  const int tid = ly * TXP + lx;
+  const int x = tx0 + 2 * lx, y = ty0 + ly;
+  const bool act = (x < nx) && (y < ny);  // nx even: the pair is inside when its first point is
+  const i64 col = (i64)wrapi(y, ny) * nx + wrapi(x, nx);
+
+  // halo pair owned by this thread: 2 TYP x-halo pairs, then 2 R rows of TXP pairs
+  int hrow = -1, hcs = 0;
+  i64 hcol = 0;
+  if (tid < 2 * TYP) {
+    const int side = tid / TYP, row = tid % TYP;
+    hrow = row + R;
+    hcs = side == 0 ? 0 : PW + 2;
+    hcol = (i64)wrapi(ty0 + row, ny) * nx + wrapi(side == 0 ? tx0 - 2 : tx0 + PW, nx);
+  } else if (tid < 2 * TYP + 2 * R * TXP) {
+    const int u = tid - 2 * TYP;
+    const int side = u / (R * TXP), r = u % (R * TXP);
+    const int d = r / TXP, c = r % TXP;
+    hrow = side == 0 ? d : TYP + R + d;
+    hcs = 2 + 2 * c;
+    hcol = (i64)wrapi(side == 0 ? ty0 - R + d : ty0 + TYP + d, ny) * nx + wrapi(tx0 + 2 * c, nx);
+  }
+  const int cx = 2 + 2 * lx, cy = ly + R;
+
+  const int a_first = z0 - R, a_last = z1 + R;
+  int zi = a_first;
+  int zw = wrapi(a_first, nz);
+  auto issue_next = [&](int k) {
+    if (zi < a_last) {
+      Stage<R, HIST>& g = ring[k];
+      const i64 zo = (i64)zw * pl;
+      cp_async<8>(&g.w[cy][cx], w + zo + col);
+      if (hrow >= 0) cp_async<8>(&g.w[hrow][hcs], w + zo + hcol);
+      if constexpr (HIST) {
+        cp_async<8>(&g.s[cy][cx], wp + zo + col);
+        if (hrow >= 0) cp_async<8>(&g.s[hrow][hcs], wp + zo + hcol);
+      }
+      if (zi >= z0 && zi < z1) {
+        cp_async<8>(&g.v[ly][2 * lx], V + zo + col);
+        if constexpr (HIST) cp_async<8>(&g.dv[ly][2 * lx], dVp + zo + col);
+      }
+    }
+    cp_commit();
+    ++zi;
+    zw = (zw + 1 == nz) ? 0 : zw + 1;
+  };
+#pragma unroll
+  for (int k = 0; k <= PFP; ++k) issue_next(k);
+
+  float2 qw[S], qs[S];
+#pragma unroll
+  for (int j = 0; j < S; ++j) qw[j] = qs[j] = splat(0.f);
+  K2 kww{}, kzw{}, kzz{}, kkx{}, kky{}, kkz{};
+  float2 ahw = splat(0.f), ass = splat(0.f), asb = splat(0.f), asw = splat(0.f), abb = splat(0.f),
+         abw = splat(0.f);
+  // -1/2 times the stencil scales, applied in FP32 to form H w (the sums use the raw differences)
+  const float2 cxk = splat(-0.5f * a.ihx2), cyk = splat(-0.5f * a.ihy2), czk = splat(-0.5f * a.ihz2);
+  const float2 nsig = splat(-sigp);
+  const bool scale_out = a.out_scale != 1.f;
+  const float2 oscale = splat(a.out_scale);
+  const i64 zpl0 = (i64)z0 * pl;
+
+  for (int base = a_first; base < a_last; base += S) {
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      const int pa = base + k;
+      if (pa >= a_last) break;
+      cp_wait<PFP>();
+      {
+        // plane pa has landed for this thread's own copies: queue its centre
+        // values and convert the cells this thread copied
+        Stage<R, HIST>& g = ring[k];
+        const float2 wc = lds2(&g.w[cy][cx]);
+        qw[k] = wc;
+        if constexpr (HIST) {
+          const float2 pc = lds2(&g.s[cy][cx]);
+          const float2 sc = sub2(wc, pc);
+          sts2(&g.s[cy][cx], sc);
+          qs[k] = sc;
+          if (hrow >= 0) sts2(&g.s[hrow][hcs], sub2(lds2(&g.w[hrow][hcs]), lds2(&g.s[hrow][hcs])));
+          if (pa >= z0 && pa < z1) sts2(&g.dv[ly][2 * lx], mul2(lds2(&g.dv[ly][2 * lx]), pc));
+        }
+      }
+      __syncthreads();
+      issue_next((k + PFP + 1) % S);
+      const int z = pa - R;
+      if (z < z0 || !act) continue;
+      const int iz = (k + S - R) % S;  // queue slot and ring stage of plane z
+      const Stage<R, HIST>& g = ring[iz];
+      const float2 c = qw[iz];
+      float2 ex, ey, ez;
+      second_diffs<R>(c, lds2(&g.w[cy][cx - 2]), lds2(&g.w[cy][cx + 2]), lds2(&g.w[cy - 1][cx]),
+                      lds2(&g.w[cy + 1][cx]), R == 2 ? lds2(&g.w[cy - 2][cx]) : c,
+                      R == 2 ? lds2(&g.w[cy + 2][cx]) : c, qw[(iz + S - 1) % S], qw[(iz + 1) % S],
+                      qw[(iz + S - 2) % S], qw[(iz + 2) % S], ex, ey, ez);
+      const float2 vv = lds2(&g.v[ly][2 * lx]);
+      float2 h;
+      if (CUBIC) {
+        const float2 e = add2(add2(ex, ey), ez);
+        h = fma2(vv, c, mul2(cxk, e));
+        kkx.add_prod(c, e);
+      } else {
+        h = fma2(vv, c, fma2(cxk, ex, fma2(cyk, ey, mul2(czk, ez))));
+        kkx.add_prod(c, ex);
+        kky.add_prod(c, ey);
+        kkz.add_prod(c, ez);
+      }
+      if (hw) {
+        const i64 idx = zpl0 + (i64)(z - z0) * pl + col;
+        *reinterpret_cast<float2*>(hw + idx) = scale_out ? mul2(oscale, h) : h;
+      }
+      const float2 zp = fma2(nsig, c, h);
+      kww.add_prod(c, c);
+      ahw = fma2(h, c, ahw);
+      kzw.add_prod(zp, c);
+      kzz.add_prod(zp, zp);
+      if constexpr (HIST) {
+        const float2 sc = qs[iz];
+        float2 fx, fy, fz;
+        second_diffs<R>(sc, lds2(&g.s[cy][cx - 2]), lds2(&g.s[cy][cx + 2]), lds2(&g.s[cy - 1][cx]),
+                        lds2(&g.s[cy + 1][cx]), R == 2 ? lds2(&g.s[cy - 2][cx]) : sc,
+                        R == 2 ? lds2(&g.s[cy + 2][cx]) : sc, qs[(iz + S - 1) % S], qs[(iz + 1) % S],
+                        qs[(iz + S - 2) % S], qs[(iz + 2) % S], fx, fy, fz);
+        float2 hs;
+        if (CUBIC)
+          hs = fma2(vv, sc, mul2(cxk, add2(add2(fx, fy), fz)));
+        else
+          hs = fma2(vv, sc, fma2(cxk, fx, fma2(cyk, fy, mul2(czk, fz))));
+        hs = add2(hs, lds2(&g.dv[ly][2 * lx]));  // + (V - V') w'
+        const float2 b = fma2(nsig, sc, hs);      // (hw - hw') - sigma' s
+        ass = fma2(sc, sc, ass);
+        asb = fma2(sc, b, asb);
+        asw = fma2(sc, c, asw);
+        abb = fma2(b, b, abb);
+        abw = fma2(b, c, abw);
+      }
+    }
+  }
+  cp_wait<0>();
+
+  if (a.tilepart == nullptr) return;
+  const int lane = tid & 31, warp = tid >> 5;
+  double fin[NPT];
+  auto dsum = [](float2 v) { return (double)v.x + (double)v.y; };
+  fin[P_WW] = kww.value();
+  fin[P_HW] = dsum(ahw);
+  fin[P_ZW] = kzw.value();
+  fin[P_ZZ] = kzz.value();
+  fin[P_KX] = kkx.value();
+  fin[P_KY] = CUBIC ? 0.0 : kky.value();
+  fin[P_KZ] = CUBIC ? 0.0 : kkz.value();
+  fin[P_SS] = dsum(ass);
+  fin[P_SB] = dsum(asb);
+  fin[P_SW] = dsum(asw);
+  fin[P_BB] = dsum(abb);
+  fin[P_BW] = dsum(abw);
+#pragma unroll
+  for (int k = 0; k < NPT; ++k) {
+    double v = fin[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][k] = v;
+  }
+  __syncthreads();
+  if (tid < NPT) {
+    double v = 0.0;
+#pragma unroll
+    for (int wi = 0; wi < NTP / 32; ++wi) v += red[wi][tid];
+    const int ntile = gridDim.x * gridDim.y;
+    const int tile = blockIdx.y * gridDim.x + blockIdx.x;
+    a.tilepart[((i64)orb * ntile + tile) * NPT + tid] = v;
+  }
+}
+
+template <int R, bool HIST>
+size_t smem_bytes() {
+  return sizeof(Stage<R, HIST>) * (size_t)(R + 2 + PFP);
+}
+
+}  // namespace pk
+
 template <typename T, int R>
 size_t apply_pair_smem() {
   return sizeof(PStage<T, R>) * (size_t)(R + 2 + PPF);
@@ -601,6 +905,22 @@ size_t apply_smem() {
 }  // namespace
 
 void configure_apply_h() {
+  cudaFuncSetAttribute(pk::k_apply_h_pk<1, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)pk::smem_bytes<1, false>());
+  cudaFuncSetAttribute(pk::k_apply_h_pk<1, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)pk::smem_bytes<1, false>());
+  cudaFuncSetAttribute(pk::k_apply_h_pk<1, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)pk::smem_bytes<1, true>());
+  cudaFuncSetAttribute(pk::k_apply_h_pk<1, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)pk::smem_bytes<1, true>());
+  cudaFuncSetAttribute(pk::k_apply_h_pk<2, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)pk::smem_bytes<2, false>());
+  cudaFuncSetAttribute(pk::k_apply_h_pk<2, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)pk::smem_bytes<2, false>());
+  cudaFuncSetAttribute(pk::k_apply_h_pk<2, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)pk::smem_bytes<2, true>());
+  cudaFuncSetAttribute(pk::k_apply_h_pk<2, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)pk::smem_bytes<2, true>());
   cudaFuncSetAttribute(k_apply_h_pair<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)apply_pair_smem<float, 1>());
   cudaFuncSetAttribute(k_apply_h_pair<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -617,11 +937,22 @@ void configure_apply_h() {
                        (int)apply_smem<double, 2>());
 }
 
-// tile width in x: paired kernel (two points per thread) for even nx
-static int tile_w(int nx) { return (nx % 2 == 0) ? PTX : TX; }
+// Tile of a launch: the pk kernel for FP32 with even nx (32 x 16 points,
+// 16 x 16 threads), the paired kernel for FP64 with even nx (64 x 8 points),
+// the scalar kernel for odd nx (32 x 8 points).
+enum TileKind { TILE_SCALAR = 0, TILE_PAIR = 1, TILE_PACKED = 2 };
+struct TileShape {
+  int kind, tw, th, bx, by;
+};
+static TileShape tile_shape(int nx, int elem_bytes) {
+  if (nx % 2 == 0 && elem_bytes == 4) return {TILE_PACKED, pk::PW, pk::TYP, pk::TXP, pk::TYP};
+  if (nx % 2 == 0) return {TILE_PAIR, PTX, TY, TX, TY};
+  return {TILE_SCALAR, TX, TY, TX, TY};
+}
 
-int apply_h_ntile(int nx, int ny, int nz, int N, int* nzc_out) {
-  const int ntx = (nx + tile_w(nx) - 1) / tile_w(nx), nty = (ny + TY - 1) / TY;
+int apply_h_ntile(int nx, int ny, int nz, int N, int elem_bytes, int* nzc_out) {
+  const TileShape ts = tile_shape(nx, elem_bytes);
+  const int ntx = (nx + ts.tw - 1) / ts.tw, nty = (ny + ts.th - 1) / ts.th;
   const long long base = (long long)ntx * nty * N;
   int nzc = 1;
   // enough CTAs to fill the GPU several times, with z sweeps of >= 8 planes
@@ -634,13 +965,37 @@ template <typename T>
 void launch_apply_h(const ApplyArgs<T>& a0, int order, cudaStream_t s, int* ntile_out) {
   ApplyArgs<T> a = a0;
   int nzc = 1;
-  const int ntile = apply_h_ntile(a.nx, a.ny, a.nz, a.N, &nzc);
+  const int ntile = apply_h_ntile(a.nx, a.ny, a.nz, a.N, (int)sizeof(T), &nzc);
   a.nzc = nzc;
-  const int tw = tile_w(a.nx);
-  const int ntx = (a.nx + tw - 1) / tw, nty = (a.ny + TY - 1) / TY;
-  dim3 grid(ntx * nty, nzc, a.N), block(TX, TY);
+  const TileShape ts = tile_shape(a.nx, (int)sizeof(T));
+  const int ntx = (a.nx + ts.tw - 1) / ts.tw, nty = (a.ny + ts.th - 1) / ts.th;
+  dim3 grid(ntx * nty, nzc, a.N), block(ts.bx, ts.by);
   prof_begin("apply_h", s);
-  if (tw == PTX) {
+  if constexpr (sizeof(T) == 4) {
+    if (ts.kind == TILE_PACKED) {
+      const bool hist = a.mode == 0;
+      const bool cubic = a.cubic != 0;
+#define POU_PK(R_, H_, C_) pk::k_apply_h_pk<R_, H_, C_><<<grid, block, pk::smem_bytes<R_, H_>(), s>>>(a)
+      if (order == 2) {
+        if (hist) {
+          if (cubic) POU_PK(1, true, true); else POU_PK(1, true, false);
+        } else {
+          if (cubic) POU_PK(1, false, true); else POU_PK(1, false, false);
+        }
+      } else {
+        if (hist) {
+          if (cubic) POU_PK(2, true, true); else POU_PK(2, true, false);
+        } else {
+          if (cubic) POU_PK(2, false, true); else POU_PK(2, false, false);
+        }
+      }
+#undef POU_PK
+      prof_end(s);
+      if (ntile_out) *ntile_out = ntile;
+      return;
+    }
+  }
+  if (ts.kind == TILE_PAIR) {
     if (order == 2)
       k_apply_h_pair<T, 1><<<grid, block, apply_pair_smem<T, 1>(), s>>>(a);
     else

@@ -236,6 +236,12 @@ double stencil_scale(const pou_ctx* c, int a) {
   return c->cfg.stencil_order == 2 ? 1.0 / h2 : 1.0 / (12.0 * h2);
 }
 
+// 1 when the three per-axis stencil scales are equal, so that the H-apply may
+// keep one kinetic sum for all axes (the FP64 coefficients are then equal).
+int cubic_scales(const pou_ctx* c) {
+  return stencil_scale(c, 0) == stencil_scale(c, 1) && stencil_scale(c, 1) == stencil_scale(c, 2) ? 1 : 0;
+}
+
 // Second Cholesky-QR pass on the block just written to W[1-cur], gated on
 // st->reorth (FP32 form only).
 template <typename T>
@@ -347,6 +353,7 @@ void enqueue_diag(pou_ctx* c) {
   aa.ihx2 = (T)stencil_scale(c, 0);
   aa.ihy2 = (T)stencil_scale(c, 1);
   aa.ihz2 = (T)stencil_scale(c, 2);
+  aa.cubic = cubic_scales(c);
   int ntile = 0;
   launch_apply_h<T>(aa, c->cfg.stencil_order, s, &ntile);
   CtrlArgs k{};
@@ -465,6 +472,7 @@ void enqueue_pass(pou_ctx* c) {
   aa.ihx2 = (T)stencil_scale(c, 0);
   aa.ihy2 = (T)stencil_scale(c, 1);
   aa.ihz2 = (T)stencil_scale(c, 2);
+  aa.cubic = cubic_scales(c);
   int ntile = 0;
   launch_apply_h<T>(aa, c->cfg.stencil_order, s, &ntile);
   // accept / reject
@@ -571,6 +579,7 @@ pou_status init_from_staged(pou_ctx* c) {
   aa.ihx2 = (T)stencil_scale(c, 0);
   aa.ihy2 = (T)stencil_scale(c, 1);
   aa.ihz2 = (T)stencil_scale(c, 2);
+  aa.cubic = cubic_scales(c);
   int ntile = 0;
   launch_apply_h<T>(aa, c->cfg.stencil_order, s, &ntile);
   CtrlArgs k{};
@@ -713,6 +722,7 @@ pou_status eval_block(pou_ctx* c, const T* U, T* HUout, T scale, pou_energy_term
   aa.ihx2 = (T)stencil_scale(c, 0);
   aa.ihy2 = (T)stencil_scale(c, 1);
   aa.ihz2 = (T)stencil_scale(c, 2);
+  aa.cubic = cubic_scales(c);
   int ntile = 0;
   launch_apply_h<T>(aa, c->cfg.stencil_order, s, &ntile);
   pou_status e = check_launch(c, "evaluation kernels");
@@ -913,7 +923,7 @@ static pou_status create_buffers(pou_ctx* c) {
   DALLOC(c->vext, c->ng * sizeof(double));
   CK(cudaMemsetAsync(c->vext, 0, c->ng * sizeof(double), c->stream));
   DALLOC(c->work, c->ng * sizeof(double2));
-  c->ntile = apply_h_ntile(c->nx, c->ny, c->nz, c->N, nullptr);
+  c->ntile = apply_h_ntile(c->nx, c->ny, c->nz, c->N, (int)c->esz, nullptr);
   DALLOC(c->tilepart, (size_t)c->N * c->ntile * NPT * sizeof(double));
   c->neblk_max = (int)std::max<long long>((long long)num_sms() * 4, (long long)c->nz * c->ny);
   DALLOC(c->epart, (size_t)c->neblk_max * NE * sizeof(double));

@@ -83,10 +83,11 @@ struct ApplyArgs {
   T out_scale;
   int N, nx, ny, nz, nzc;
   T ihx2, ihy2, ihz2;
+  int cubic;            // 1: the three stencil scales are equal (FP64), so one kinetic sum serves
 };
 template <typename T>
 void launch_apply_h(const ApplyArgs<T>& a, int order, cudaStream_t s, int* ntile_out);
-int apply_h_ntile(int nx, int ny, int nz, int N, int* nzc_out);
+int apply_h_ntile(int nx, int ny, int nz, int N, int elem_bytes, int* nzc_out);
 
 // ---------------------------------------------------------------- gram / rotation
 template <typename T>
