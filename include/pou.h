@@ -97,6 +97,10 @@ typedef struct {
                          (Sec. 3.3: Sigma = <W^T H W>, P^T Sigma P diagonal, W <- W P);
                          0 = off */
   void* stream;       /* cudaStream_t to run on; NULL: the library creates one */
+  int direction;      /* search direction (Sec. 3.1): 0 (default) Opt-Par, z_i = H w_i - sigma_ii w_i;
+                         1 OptM-QR, the comparison method of Table 1, Z = HW - W Sigma with the full
+                         Sigma = <W^T H W>, its own Barzilai-Borwein differences Y = Z - Z'.  1 needs
+                         n_org = 1 and n_diag = 0, and two more orbital blocks of device memory */
 } pou_config;
 
 #define POU_MAX_N 512      /* FP32 form (without the subspace diagonalisation) */

@@ -227,7 +227,13 @@ __global__ void k_gram_reduce(GramReduceArgs a) {
     for (int k = 0; k < a.nsplit; ++k) s += a.split[off + k * stride];
   }
   s *= a.dV;
-  if (a.trial && r == c) {
+  if (a.trial == 2 && r == c) {
+    // OptM-QR: the trial column w - tau z, z the direction block; FP64 sums
+    // of the kernel that formed z
+    const double tau = a.st->tau_trial;
+    const double* dp = a.dpart + (i64)r * 3;
+    s = a.dV * (dp[0] - 2.0 * tau * dp[1] + tau * tau * dp[2]);
+  } else if (a.trial && r == c) {
     // FP64 norm of the trial column a w - t hw (FP64 coefficients, as both
     // rotations form the trial point) from the H-apply sums of W[cur]:
     //   a w - t hw = w - t z_e,  z_e = hw - s_e w,  s_e = (a - 1) / t,

@@ -119,6 +119,14 @@ struct pou_ctx {
   double* evec;      // eigenvector scratch of the subspace diagonalisation
   float* rimg;       // split R^-1 image of the FP32 tensor-core rotation (N > 128)
   void* dv;          // V(trial) - V(current), working type (written by the potential pass)
+  // OptM-QR direction (config direction = 1): Z = HW - W Sigma per pair, the
+  // direction kernel's partials, the per-orbital sums of the trial diagonal,
+  // and a zero sigma (the trial kernels then form W - tau Z)
+  void* Z[2];
+  double* dir_opart;
+  double* dir_bpart;
+  double* dir_dpart;
+  double* zero_sigma;
   State* st;
   double* hist_E;
   double* hist_tau;
@@ -375,17 +383,81 @@ void enqueue_diag(pou_ctx* c) {
 }
 
 // ------------------------------------------------------------- one pass
+// OptM-QR (Sec. 3.1): on the first pass of a step, Sigma = <W^T HW> of the
+// current pair, Z = HW - W Sigma with its sums, and the step's tau and ||Z||^2.
 template <typename T>
-void enqueue_pass(pou_ctx* c) {
+void enqueue_direction_full(pou_ctx* c) {
   cudaStream_t s = c->stream;
-  if (c->cfg.n_diag > 0) enqueue_diag<T>(c);
-  // trial block Wt = W - tau Z from the current pair, Gram matrix
   GramArgs<T> g{};
   g.st = c->st;
   for (int k = 0; k < 2; ++k) {
     g.W[k] = tp<T>(c->W[k]);
     g.HW[k] = tp<T>(c->HW[k]);
-    g.sigma[k] = c->sigma[k];
+  }
+  g.src_cur_pair = 1;
+  g.gate = 4;
+  g.ng = c->ng;
+  g.N = c->N;
+  g.split = c->split;
+  launch_gram<T>(g, s);
+  int nsplit, npair;
+  i64 chunk;
+  gram_layout<T>(c->ng, c->N, true, &nsplit, &npair, &chunk);
+  GramReduceArgs r{};
+  r.st = c->st;
+  r.split = c->split;
+  r.nsplit = nsplit;
+  r.npair = npair;
+  r.ST = gram_supertile<T>();
+  r.N = c->N;
+  r.general = 1;
+  r.dV = c->dV;
+  r.S = c->S;
+  r.gate = 4;
+  launch_gram_reduce(r, s);
+  DirArgs<T> d{};
+  d.st = c->st;
+  for (int k = 0; k < 2; ++k) {
+    d.W[k] = tp<T>(c->W[k]);
+    d.HW[k] = tp<T>(c->HW[k]);
+    d.Z[k] = tp<T>(c->Z[k]);
+  }
+  d.Sig = c->S;
+  d.opart = c->dir_opart;
+  d.bpart = c->dir_bpart;
+  d.ng = c->ng;
+  d.N = c->N;
+  launch_direction<T>(d, s);
+  DirCtrlArgs k{};
+  k.st = c->st;
+  k.opart = c->dir_opart;
+  k.bpart = c->dir_bpart;
+  k.dpart = c->dir_dpart;
+  k.nblk = direction_grid(c->ng);
+  k.N = c->N;
+  k.dV = c->dV;
+  k.tau0 = c->tau0;
+  k.tau_min = c->cfg.tau_min;
+  k.tau_max = c->cfg.tau_max;
+  k.bb_variant = c->cfg.bb_variant;
+  launch_direction_control(k, s);
+}
+
+template <typename T>
+void enqueue_pass(pou_ctx* c) {
+  cudaStream_t s = c->stream;
+  if (c->cfg.n_diag > 0) enqueue_diag<T>(c);
+  const bool full = c->cfg.direction == 1;
+  if (full) enqueue_direction_full<T>(c);
+  // trial block Wt = W - tau Z from the current pair, Gram matrix
+  // the trial point (1 + tau sigma_ii) w - tau hw of Opt-Par; OptM-QR hands
+  // the kernels Z and a zero sigma, so that they form w - tau z
+  GramArgs<T> g{};
+  g.st = c->st;
+  for (int k = 0; k < 2; ++k) {
+    g.W[k] = tp<T>(c->W[k]);
+    g.HW[k] = full ? tp<T>(c->Z[k]) : tp<T>(c->HW[k]);
+    g.sigma[k] = full ? c->zero_sigma : c->sigma[k];
   }
   g.trial = 1;
   g.gate = 3;  // skipped on the intermediate steps of Algorithm M (n_org > 1)
@@ -412,7 +484,8 @@ void enqueue_pass(pou_ctx* c) {
   // the FP64 coefficients (the FP32 one as a double-float, hi + lo), so the
   // diagonal is the FP64 norm of (1 + tau sigma) w - tau hw from the
   // H-apply sums.
-  r.trial = 1;
+  r.trial = full ? 2 : 1;
+  r.dpart = c->dir_dpart;
   for (int k = 0; k < 2; ++k) {
     r.sigma[k] = c->sigma[k];
     r.part[k] = c->part[k];
@@ -426,8 +499,8 @@ void enqueue_pass(pou_ctx* c) {
   ra.st = c->st;
   for (int k = 0; k < 2; ++k) {
     ra.W[k] = tp<T>(c->W[k]);
-    ra.HW[k] = tp<T>(c->HW[k]);
-    ra.sigma[k] = c->sigma[k];
+    ra.HW[k] = full ? tp<T>(c->Z[k]) : tp<T>(c->HW[k]);
+    ra.sigma[k] = full ? c->zero_sigma : c->sigma[k];
     ra.Wout[k] = tp<T>(c->W[k]);
     ra.rho[k] = c->rho[k];
   }
@@ -816,6 +889,7 @@ void pou::configure_kernels() {
   configure_eigh();
   configure_apply_h();
   configure_gram_tc();
+  configure_direction();
   configure_rotate_tc();
   done = true;
 }
@@ -844,6 +918,7 @@ void pou_config_default(pou_config* cfg) {
   cfg->n_org = 1;
   cfg->n_diag = 0;
   cfg->stream = nullptr;
+  cfg->direction = 0;
 }
 
 static pou_status create_buffers(pou_ctx* c);
@@ -864,6 +939,9 @@ pou_status pou_create(const pou_config* cfg, pou_ctx** out) {
   if (!(cfg->rho1 >= 0.0) || cfg->max_backtrack < 0 || cfg->max_backtrack > 60) return POU_EINVAL;
   if (!(cfg->tau_min > 0.0) || !(cfg->tau_max >= cfg->tau_min)) return POU_EINVAL;
   if (cfg->n_org < 1 || cfg->n_diag < 0) return POU_EINVAL;
+  // OptM-QR direction: Algorithm E only (no n_org, no subspace diagonalisation)
+  if (cfg->direction != 0 && cfg->direction != 1) return POU_EINVAL;
+  if (cfg->direction == 1 && (cfg->n_org != 1 || cfg->n_diag != 0)) return POU_EINVAL;
   // N > 128: FP32 form only, without the subspace diagonalisation
   if (cfg->N > POU_MAX_N_FP64 && (cfg->precision != POU_FP32 || cfg->n_diag > 0)) return POU_EINVAL;
   const long long ng = (long long)cfg->n[0] * cfg->n[1] * cfg->n[2];
@@ -951,6 +1029,16 @@ static pou_status create_buffers(pou_ctx* c) {
   if (c->dt == 1 && c->N > 128) DALLOC(c->rimg, rotate_rimg_bytes(c->N));
   DALLOC(c->evec, (size_t)c->N * c->N * sizeof(double));
   DALLOC(c->dv, c->ng * c->esz);
+  if (cfg->direction == 1) {
+    DALLOC(c->Z[0], blk);
+    DALLOC(c->Z[1], blk);
+    const int dg = direction_grid(c->ng);
+    DALLOC(c->dir_opart, (size_t)dg * c->N * 3 * sizeof(double));
+    DALLOC(c->dir_bpart, (size_t)dg * 3 * sizeof(double));
+    DALLOC(c->dir_dpart, (size_t)c->N * 3 * sizeof(double));
+    DALLOC(c->zero_sigma, (size_t)c->N * sizeof(double));
+    CK(cudaMemsetAsync(c->zero_sigma, 0, (size_t)c->N * sizeof(double), c->stream));
+  }
   DALLOC(c->st, sizeof(State));
   CK(cudaMemsetAsync(c->st, 0, sizeof(State), c->stream));
   DALLOC(c->hist_E, HIST_MAX * sizeof(double));
@@ -969,7 +1057,8 @@ void pou_destroy(pou_ctx* c) {
   void* ptrs[] = {c->W[0], c->W[1], c->HW[0], c->HW[1], c->V[0], c->V[1], c->rho[0], c->rho[1],
                   c->sigma[0], c->sigma[1], c->part[0], c->part[1], c->vext, c->work, c->tilepart,
                   c->epart, c->S, c->Rinv, c->split, c->evec, c->dv, c->st, c->hist_E, c->hist_tau, c->info,
-                  c->dR, c->dZ, c->tabs.gx, c->fpart, c->ublock, c->gblock, c->rho_e, c->V64_e, c->rimg};
+                  c->dR, c->dZ, c->tabs.gx, c->fpart, c->ublock, c->gblock, c->rho_e, c->V64_e, c->rimg,
+                  c->Z[0], c->Z[1], c->dir_opart, c->dir_bpart, c->dir_dpart, c->zero_sigma};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->dt == 1) {
@@ -1337,8 +1426,11 @@ struct BlobHeader {
 pou_status pou_get_state(pou_ctx* c, void* blob, size_t* size) {
   if (!c || !size) return POU_EINVAL;
   const size_t blk = (size_t)c->N * c->ng * c->esz;
+  // OptM-QR also keeps the previous iterate and its direction (its next
+  // Barzilai-Borwein step differences against them)
   const size_t need = sizeof(BlobHeader) + sizeof(State) + 2 * HIST_MAX * sizeof(double) +
-                      (size_t)c->N * (NP + 1) * sizeof(double) + 2 * blk + 2 * c->ng * sizeof(double);
+                      (size_t)c->N * (NP + 1) * sizeof(double) + 2 * blk + 2 * c->ng * sizeof(double) +
+                      (c->cfg.direction == 1 ? 2 * blk : 0);
   if (!blob) {
     *size = need;
     return POU_OK;
@@ -1378,6 +1470,12 @@ pou_status pou_get_state(pou_ctx* c, void* blob, size_t* size) {
   CK(cudaMemcpy(p, c->rho[cur], c->ng * sizeof(double), cudaMemcpyDeviceToHost));
   p += c->ng * sizeof(double);
   CK(cudaMemcpy(p, c->V64[cur], c->ng * sizeof(double), cudaMemcpyDeviceToHost));
+  p += c->ng * sizeof(double);
+  if (c->cfg.direction == 1) {
+    CK(cudaMemcpy(p, c->W[1 - cur], blk, cudaMemcpyDeviceToHost));
+    p += blk;
+    CK(cudaMemcpy(p, c->Z[1 - cur], blk, cudaMemcpyDeviceToHost));
+  }
   *size = need;
   return POU_OK;
 }
@@ -1414,6 +1512,14 @@ pou_status pou_set_state(pou_ctx* c, const void* blob, size_t size) {
   CK(cudaMemcpy(c->rho[cur], p, c->ng * sizeof(double), cudaMemcpyHostToDevice));
   p += c->ng * sizeof(double);
   CK(cudaMemcpy(c->V64[cur], p, c->ng * sizeof(double), cudaMemcpyHostToDevice));
+  p += c->ng * sizeof(double);
+  if (c->cfg.direction == 1) {
+    if ((long long)size < h.bytes || h.bytes < (long long)((p - static_cast<const char*>(blob)) + 2 * blk))
+      return fail(c, POU_EINVAL, "state blob lacks the OptM-QR history");
+    CK(cudaMemcpy(c->W[1 - cur], p, blk, cudaMemcpyHostToDevice));
+    p += blk;
+    CK(cudaMemcpy(c->Z[1 - cur], p, blk, cudaMemcpyHostToDevice));
+  }
   if (c->dt == 1)
     launch_convert_f64_f32(c->V64[cur], static_cast<float*>(c->V[cur]), c->ng, c->stream);
   CK(cudaMemcpy(c->st, &hs, sizeof hs, cudaMemcpyHostToDevice));

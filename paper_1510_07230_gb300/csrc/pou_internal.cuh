@@ -60,11 +60,13 @@ struct State {
 
 // Gate of the optional kernels of a pass: 0 always run, 1 second Cholesky-QR
 // pass (State::reorth), 2 subspace diagonalisation (State::diag_now), 3 the
-// trial is orthonormalised (State::orth_now; Algorithm M with n_org > 1).
+// trial is orthonormalised (State::orth_now; Algorithm M with n_org > 1), 4
+// first trial of a step (State::s == 0; the OptM-QR direction).
 __device__ __forceinline__ bool gate_open(const State* st, int gate) {
   if (gate == 0) return true;
   if (gate == 1) return st->reorth != 0;
   if (gate == 2) return st->diag_now != 0;
+  if (gate == 4) return st->s == 0;
   return st->orth_now != 0;
 }
 
@@ -131,8 +133,10 @@ struct GramReduceArgs {
   int general;          // 1: all blocks computed (A^T B); 0: upper super-tiles, symmetric
   double dV;
   double* S;            // N*N
-  // diagonal replacement for the trial Gram (iteration mode)
+  // diagonal replacement for the trial Gram (iteration mode): 1 from the
+  // H-apply sums (Opt-Par), 2 from the OptM-QR direction sums (dpart)
   int trial;
+  const double* dpart;  // [N][3]: <w,w>, <w,z>, <z,z> of the OptM-QR direction
   const double* sigma[2];
   const double* part[2];
   int gate;             // see gate_open
@@ -182,6 +186,36 @@ void launch_convert_f64_f32(const double* in, float* out, i64 n, cudaStream_t s)
 void launch_convert_f32_f64(const float* in, double* out, i64 n, cudaStream_t s);
 template <typename T>
 void launch_scale_copy(const T* in, T* out, T scale, i64 n, cudaStream_t s);
+
+// ---------------------------------------------------------------- OptM-QR direction
+constexpr int POU_DIR_MAX_N = 512;
+constexpr int POU_DIR_MAX_N_FP64 = 128;
+template <typename T>
+struct DirArgs {
+  State* st;
+  const T* W[2];
+  const T* HW[2];
+  T* Z[2];              // Z[cur] written, Z[1-cur] the previous step's
+  const double* Sig;    // N*N, Sig[i][j] = <w_i, hw_j> of the current pair
+  double* opart;        // [grid][N][3]
+  double* bpart;        // [grid][3]
+  i64 ng;
+  int N;
+};
+struct DirCtrlArgs {
+  State* st;
+  const double* opart;
+  const double* bpart;
+  double* dpart;        // [N][3]
+  int nblk, N;
+  double dV, tau0, tau_min, tau_max;
+  int bb_variant;
+};
+int direction_grid(i64 ng);
+void configure_direction();
+template <typename T>
+void launch_direction(const DirArgs<T>& a, cudaStream_t s);
+void launch_direction_control(const DirCtrlArgs& a, cudaStream_t s);
 
 // ---------------------------------------------------------------- cholesky
 // reorth_thr > 0: first pass, sets st->reorth when max|S - I| > reorth_thr;

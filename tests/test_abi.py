@@ -44,7 +44,7 @@ def test_config_default_is_the_papers_constants(pou):
 
 @pytest.mark.parametrize("field,value", [
     ("N", 0), ("N", 129), ("N", 513), ("stencil_order", 3), ("precision", 7), ("bb_variant", 0),
-    ("delta", 1.5), ("eta", -0.1), ("n_org", 0), ("n_diag", -1), ("tau_min", 0.0),
+    ("delta", 1.5), ("eta", -0.1), ("n_org", 0), ("n_diag", -1), ("tau_min", 0.0), ("direction", 2),
 ])
 def test_invalid_configs_rejected_before_touching_the_device(pou, field, value):
     cfg = pou.make_config(16, 8.0, 4)
