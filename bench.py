@@ -43,6 +43,7 @@ def metric_name(w, precision="fp32"):
     form = "mixed form" if precision == "fp32" else "FP64 form"
     return f"outer iterations/s ({w.n}^3, N={w.N}, {7 if w.order == 2 else 13}-point, {form})"
 UNIT = "iterations/s"
+HIST_ENTRIES = 16384  # energies the library keeps per run (pou_get_history)
 
 
 def parse():
@@ -67,6 +68,13 @@ def parse():
     ap.add_argument("--ttt-refine-max", type=int, default=4000, help="cap of the FP64 refinement of --ttt")
     ap.add_argument("--ttt-conv-rel", type=float, default=1e-10,
                     help="--ttt: the refinement stops when E falls by less than this times |E| over 100 steps")
+    ap.add_argument("--ttt-small", default="l20_g96_n32",
+                    help="workload of the time-to-1e-6 Ha run the default line carries ('' to skip)")
+    ap.add_argument("--table1", action="store_true",
+                    help="Opt-Par vs OptM-QR (Table 1): iterations and time to ||grad E|| < --table1-grad, FP64 form")
+    ap.add_argument("--table1-workload", default="l20_g96_n32")
+    ap.add_argument("--table1-grad", type=float, default=1e-6)
+    ap.add_argument("--table1-max", type=int, default=8000)
     return ap.parse_args()
 
 
@@ -189,43 +197,84 @@ sys.path.insert(0, %(root)r)
 import numpy as np
 from oracle import pou_oracle as O
 from paper_1510_07230_gb300 import inputs
-w, R, Z = inputs.WORKLOADS[%(wl)r], None, None
+w = inputs.WORKLOADS[%(wl)r]
 R, Z = inputs.atoms(w.seed, w.n_atoms, w.L, w.z_recipe)
-Ns = %(ns)d
-U0 = inputs.random_orbitals(w.seed, w.N, (w.n, w.n, w.n), count=Ns)
-cfg = O.cubic(w.n, w.L, order=w.order, N=Ns)
-vext = O.vext_gaussians(cfg, R, Z, w.width)
-st = O.initial_state(U0, vext, cfg)
-times = []
-for k in range(%(steps)d):
-    t = time.perf_counter()
-    O.iterate(st, vext, cfg)
-    times.append(time.perf_counter() - t)
-print(json.dumps({"times": times}))
+out = {}
+for Ns, steps in %(legs)r:
+    U0 = inputs.random_orbitals(w.seed, w.N, (w.n, w.n, w.n), count=Ns)
+    cfg = O.cubic(w.n, w.L, order=w.order, N=Ns)
+    vext = O.vext_gaussians(cfg, R, Z, w.width)
+    st = O.initial_state(U0, vext, cfg)
+    times = []
+    for k in range(steps):
+        t = time.perf_counter()
+        O.iterate(st, vext, cfg)
+        times.append(time.perf_counter() - t)
+    out[str(Ns)] = times
+    del st, U0
+print(json.dumps(out))
 """
 
 
-def run_oracle_sample(workload, ns, steps):
+def host_resources():
+    """Cores this process may use, the BLAS thread count given to the oracle,
+    and host RAM (GB)."""
+    cores = len(os.sched_getaffinity(0))
+    ram = None
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemTotal:"):
+                    ram = round(int(line.split()[1]) / 1024 ** 2, 1)
+    except OSError:
+        pass
+    return cores, ram
+
+
+def run_oracle_sample(workload, legs):
+    """Oracle iterations on the first Ns orbitals of the workload, for each
+    (Ns, steps) leg; returns {Ns: [seconds per iteration]}.  The BLAS calls
+    (Gram, Cholesky, triangular solve) get every core of the process; the
+    stencil and FFT parts of NumPy run on one."""
+    cores, _ = host_resources()
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[k] = "1"
-    code = ORACLE_SAMPLE_CODE % {"root": ROOT, "wl": workload, "ns": ns, "steps": steps}
+        env[k] = str(cores)
+    code = ORACLE_SAMPLE_CODE % {"root": ROOT, "wl": workload, "legs": [tuple(x) for x in legs]}
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
-    return json.loads(r.stdout.strip().splitlines()[-1])["times"]
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {int(k): v for k, v in d.items()}
 
 
-def cpu_baseline(workload, steps=2, ns=8):
+def extrapolate_iteration(t_small, n_small, t_big, n_big, N):
+    """Seconds per oracle iteration at N orbitals from two sample sizes, with
+    t(n) = a n + b n^2 (per-orbital work plus the N^2 Gram, Cholesky-QR and
+    rotation terms); b is clamped at zero when the samples show none."""
+    b = (t_big * n_small - t_small * n_big) / (n_big * n_big * n_small - n_small * n_small * n_big)
+    b = max(b, 0.0)
+    a = (t_small - b * n_small * n_small) / n_small
+    return a * N + b * N * N, a, b
+
+
+def cpu_baseline(workload, steps=2, ns=(8, 16)):
     w = inputs.WORKLOADS[workload]
-    ns = min(ns, w.N)
-    times = run_oracle_sample(workload, ns, steps)
-    per_iter = statistics.mean(times) * (w.N / ns)
-    return {"value": 1.0 / per_iter, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"{steps} oracle iterations on the first {ns} of the {w.N} orbitals of the same "
-                       f"{w.n}^3 workload (FP64 NumPy, 1 BLAS thread), time scaled by {w.N}/{ns}; the "
-                       f"scaling ignores the N^2 Gram/rotation terms, so this overstates the oracle rate"),
-            "seconds_measured": sum(times)}
+    n1, n2 = min(ns[0], w.N), min(ns[1], w.N)
+    times = run_oracle_sample(workload, [(n1, steps), (n2, steps)])
+    t1, t2 = statistics.mean(times[n1]), statistics.mean(times[n2])
+    if n1 == n2 == w.N:
+        per_iter, a, b = t1, None, None
+        how = f"{steps} full oracle iterations"
+    else:
+        per_iter, a, b = extrapolate_iteration(t1, n1, t2, n2, w.N)
+        how = (f"extrapolated: {steps} oracle iterations each on the first {n1} and the first {n2} of the {w.N} "
+               f"orbitals, fitted as t(n) = a n + b n^2 (a = {a:.3g} s, b = {b:.3g} s) and evaluated at n = {w.N}")
+    cores, ram = host_resources()
+    return {"value": 1.0 / per_iter, "unit": UNIT, "cores": cores, "kind": "oracle", "extrapolated": n1 != w.N,
+            "sample": f"{how}; same {w.n}^3 workload, FP64 NumPy/SciPy",
+            "blas_threads": cores, "threads_note": "BLAS calls use every core; NumPy stencils and FFTs one",
+            "host_ram_gb": ram, "seconds_measured": round(sum(times[n1]) + sum(times[n2]), 2)}
 
 
 # --------------------------------------------------------------- our arm
@@ -264,38 +313,51 @@ def run_ours(args):
     if args.prep_steps > 0:
         s.iterate(args.prep_steps)
 
-    def step(i):
-        s.iterate(1)
-        if fe > 0 and (i + 1) % fe == 0:
-            s.backward(None, 1.0, None, atoms=True)
+    def steps(k0, k):
+        """k accepted steps from step index k0, forces every fe steps; returns
+        (passes, second Cholesky-QR passes)."""
+        passes = second = 0
+        i = k0
+        while i < k0 + k:
+            n = k0 + k - i
+            if fe > 0:
+                n = min(n, fe - i % fe)
+            rep = s.iterate(n)
+            passes += rep["passes"]
+            second += rep["second_passes"]
+            i += n
+            if fe > 0 and i % fe == 0:
+                s.backward(None, 1.0, None, atoms=True)
+        return passes, second
 
-    for i in range(W):
-        step(i)
-    s.set_profiling(True)
+    steps(0, W)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clock = ClockSampler(local)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     launches0 = s.launch_count()
-    passes = 0
-    second = 0
+    # timed region: the production path (every pass replayed as one CUDA graph)
     ev0.record(stream)
-    for i in range(K):
-        rep = s.iterate(1)
-        passes += rep["passes"]
-        second += rep["second_passes"]
-        if fe > 0 and (i + 1) % fe == 0:
-            s.backward(None, 1.0, None, atoms=True)
+    passes, second = steps(W, K)
     ev1.record(stream)
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     clocks = clock.stop()
     ms = ev0.elapsed_time(ev1)
     launches = s.launch_count() - launches0
-    prof = s.profile()
-    s.set_profiling(False)
     E_final = s.energy()["total"]
     ms, value = job_rate(ms, K, world)
+    # per-kernel times: a further K steps with every kernel launched on its
+    # own between CUDA events on the library's stream (no graph replay)
+    s.set_profiling(True)
+    pw0 = time.perf_counter()
+    ppasses, psecond = steps(W + K, K)
+    torch.cuda.synchronize()
+    prof_wall = time.perf_counter() - pw0
+    prof = s.profile()
+    s.set_profiling(False)
 
     # roofline of the dominant kernel (live CUDA-event times on the library's stream)
     esz = 4 if prec == pou.FP32 else 8
@@ -311,13 +373,15 @@ def run_ours(args):
     roof = {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": (ach / peaks["hbm_gbs"]) if ach else None, "traffic": traffic_for(name, w.N * ng),
             "peak_source": f"hbm_gbs of {src}"}
+    roof["window"] = (f"{K} profiled steps after the timed region ({ppasses} passes), each kernel between CUDA "
+                      "events on the library's stream")
     kernels = {}
     # kernels of the second Cholesky-QR pass are launched every pass and return
     # at once unless the pass is taken: rates use the passes actually taken
     gated = {"gram_reorth", "rotate_reorth"}
     for k, (n_, t_) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
         b = algorithmic_bytes(k, w.N, ng, esz, w.n)
-        eff = second if k in gated else n_
+        eff = psecond if k in gated else n_
         kernels[k] = {"launches": n_, "ms_total": round(t_, 3), "share": round(t_ / sum(v[1] for v in prof.values()), 4),
                       "gbs": round(b / (t_ / eff / 1e3) / 1e9, 1) if (b and eff) else None}
         if k in gated:
@@ -344,6 +408,8 @@ def run_ours(args):
                    "state": f"after {args.prep_steps} untimed steps from the random start"},
         "passes": passes, "second_cholesky_qr_passes": second, "gpu_launches": launches, "roofline": roof,
         "kernels": kernels,
+        "profiled_window": {"steps": K, "passes": ppasses, "second_cholesky_qr_passes": psecond,
+                            "ms_per_step_profiled": prof_wall * 1e3 / K},
         "energy_final": E_final, "clocks": clocks, "input_generation_s": round(gen_s, 1),
     }
     out["_iter_kernels"] = iter_kernels
@@ -389,6 +455,11 @@ def run_ours(args):
 
     if args.ttt:
         out["time_to_1e-6"] = time_to_tolerance(pou, torch, w, R, Z, U0, stream, args)
+    if args.ttt_small and args.ttt_small != args.workload and world == 1:
+        ws, Rs, Zs, Us = inputs.workload_inputs(args.ttt_small)
+        out[f"time_to_1e-6_{args.ttt_small}"] = time_to_tolerance(pou, torch, ws, Rs, Zs, Us, stream, args)
+    if args.table1 and world == 1:
+        out["table1"] = table1(pou, torch, args, stream)
 
     if rank == 0:
         if not args.no_cpu:
@@ -419,6 +490,8 @@ def time_to_tolerance(pou, torch, w, R, Z, U0, stream, args):
     res = {}
     chunk = 50
     switch_rel, conv_rel = 3e-8, args.ttt_conv_rel
+    if max(args.ttt_max, args.ttt_fp64_max, args.ttt_refine_max) > HIST_ENTRIES:
+        raise ValueError(f"time-to-tolerance caps above {HIST_ENTRIES} steps: the energy history holds no more")
 
     def stalled(rel):
         def f(E):  # energy drop over the last 100 steps
@@ -486,32 +559,81 @@ def time_to_tolerance(pou, torch, w, R, Z, U0, stream, args):
                                 f"{float(E64b[-101] - E64b[-1]) if len(E64b) > 100 else float('nan'):.3g} Ha), "
                                 "and the FP64 form alone")
     res["switch_rule"] = f"mixed energy falls by less than {switch_rel:g} |E| over 100 steps"
-    res["workload"] = args.workload
+    res["workload"] = w.name
+    return res
+
+
+def table1(pou, torch, args, stream):
+    """Table 1's comparison on a synthetic system: Opt-Par (per-orbital
+    sigma_ii) and OptM-QR (full Sigma), both in the FP64 form from the same
+    start, to ||grad E||_F < table1_grad (Eq. gra, checked every 10 steps);
+    iterations, seconds and energy of each, and the rate of each form."""
+    w, R, Z, U0 = inputs.workload_inputs(args.table1_workload)
+    res = {"workload": w.name, "grad_tol": args.table1_grad, "cap": args.table1_max}
+    for name, d in (("opt_par", pou.OPT_PAR), ("optm_qr", pou.OPTM_QR)):
+        s = pou.Solver(w.n, w.L, w.N, order=w.order, precision=pou.FP64, stream=stream.cuda_stream,
+                       bb_variant=args.bb_variant, direction=d)
+        s.set_atoms(R, Z, w.width)
+        s.set_orbitals(U0)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        rep = s.iterate(args.table1_max, grad_tol=args.table1_grad)
+        sec = time.perf_counter() - t
+        res[name] = {"iterations": rep["iterations"], "seconds": round(sec, 3), "energy": rep["energy"],
+                     "grad_norm": rep["grad_norm"], "converged": rep["converged"] == 2,
+                     "backtracks": rep["backtracks"], "ms_per_iteration": round(sec * 1e3 / max(rep["iterations"], 1), 3)}
+        # steady-state rate of the mixed form with the same direction
+        s.close()
+        m = pou.Solver(w.n, w.L, w.N, order=w.order, precision=pou.FP32, stream=stream.cuda_stream,
+                       bb_variant=args.bb_variant, direction=d)
+        m.set_atoms(R, Z, w.width)
+        m.set_orbitals(U0)
+        m.iterate(50)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        m.iterate(200)
+        torch.cuda.synchronize()
+        res[name]["mixed_ms_per_iteration"] = round((time.perf_counter() - t) * 1e3 / 200, 3)
+        m.close()
+    res["energy_difference"] = res["optm_qr"]["energy"] - res["opt_par"]["energy"]
     return res
 
 
 # --------------------------------------------------------------- reference arm
 def run_reference(args):
+    """The oracle as it stands, on this machine's host cores: each warm-up step is
+    one oracle iteration on the first 16 orbitals of the workload, each timed
+    step one on the first 8.  ms_per_step is the time a timed step actually
+    took; value is the iteration rate of the whole N-orbital problem,
+    extrapolated from the two sample sizes (t(n) = a n + b n^2)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     w = inputs.WORKLOADS[args.workload]
-    ns = min(8, w.N)
-    total = args.warmup + args.steps
-    times = run_oracle_sample(args.workload, ns, total)
-    timed = times[args.warmup:]
-    per_iter = statistics.mean(timed) * (w.N / ns)
+    n1, n2 = min(8, w.N), min(16, w.N)
+    W = max(args.warmup, 1)
+    times = run_oracle_sample(args.workload, [(n2, W), (n1, args.steps)])
+    timed = times[n1]
+    t_small = statistics.mean(timed)
+    t_big = statistics.mean(times[n2])
+    if n1 == n2:
+        per_iter = t_small
+        how = f"each step one oracle iteration on all {w.N} orbitals"
+    else:
+        per_iter, a, b = extrapolate_iteration(t_small, n1, t_big, n2, w.N)
+        how = (f"each warm-up step one oracle iteration on the first {n2} and each timed step one on the first "
+               f"{n1} of the {w.N} orbitals of the {w.n}^3 workload; value extrapolated to {w.N} orbitals with "
+               f"t(n) = a n + b n^2 (a = {a:.3g} s, b = {b:.3g} s)")
     value = 1.0 / per_iter
-    sample = (f"each step: one oracle iteration on the first {ns} of the {w.N} orbitals of the "
-              f"{w.n}^3 workload (FP64 NumPy, 1 BLAS thread), time scaled by {w.N}/{ns}")
-    # n_gpus: the launch's GPU count (the line pairs with our arm's); the
-    # oracle itself runs on one host core, as cpu_baseline says
+    cores, ram = host_resources()
     out = {"impl": "reference", "metric": metric_name(w, args.precision), "value": value, "unit": UNIT,
-           "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_iter * 1e3,
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_small * 1e3,
+           "ms_per_step_is": f"the measured time of one timed step ({n1}-orbital sample)",
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": {"workload": args.workload, "grid": f"{w.n}^3", "N": w.N},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "extrapolated": n1 != w.N, "sample": how + "; FP64 NumPy/SciPy",
+                            "blas_threads": cores, "host_ram_gb": ram},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 

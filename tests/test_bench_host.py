@@ -64,7 +64,7 @@ def test_time_to_tolerance_protocol(monkeypatch):
     monkeypatch.setattr(bench.time, "perf_counter", lambda: next(clock))
     args = types.SimpleNamespace(ttt_max=6000, ttt_fp64_max=4000, ttt_refine_max=6000, ttt_conv_rel=1e-10,
                                  bb_variant=3, workload="fake")
-    w = types.SimpleNamespace(width=0.8)
+    w = types.SimpleNamespace(width=0.8, name="fake")
     res = bench.time_to_tolerance(pou, torch, w, None, None, 0.0, types.SimpleNamespace(cuda_stream=0), args)
     # the mixed form stalls 5e-5 above the minimum: not reached, and it stopped early
     assert not res["mixed"]["reached"] and res["mixed"]["iterations"] < 6000
@@ -109,6 +109,26 @@ def test_reference_arm_line_keeps_the_contract():
     assert d["metric"].startswith("outer iterations/s (32^3, N=4")
     assert d["config"]["workload"] == "l10_g32_n4"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
-    assert "first 4 of the 4 orbitals" in d["cpu_baseline"]["sample"]
+    assert "all 4 orbitals" in d["cpu_baseline"]["sample"] and d["cpu_baseline"]["extrapolated"] is False
+    assert d["cpu_baseline"]["cores"] == len(os.sched_getaffinity(0))
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert d["ms_per_step"] == pytest.approx(1e3 / d["value"])
+
+
+def test_oracle_time_extrapolation_keeps_the_quadratic_term():
+    """t(n) = a n + b n^2 recovered from two sample sizes and evaluated at N;
+    a negative quadratic term from noisy samples is clamped to zero."""
+    a, b = 0.4, 0.003
+    t = lambda n: a * n + b * n * n
+    per, a1, b1 = bench.extrapolate_iteration(t(8), 8, t(16), 16, 128)
+    assert per == pytest.approx(t(128)) and a1 == pytest.approx(a) and b1 == pytest.approx(b)
+    per, _, b2 = bench.extrapolate_iteration(3.3, 8, 6.5, 16, 128)
+    assert b2 == 0.0 and per == pytest.approx(3.3 / 8 * 128)
+
+
+def test_time_to_tolerance_refuses_caps_beyond_the_history():
+    args = types.SimpleNamespace(ttt_max=20000, ttt_fp64_max=4000, ttt_refine_max=4000, ttt_conv_rel=1e-10,
+                                 bb_variant=3, workload="fake")
+    with pytest.raises(ValueError):
+        bench.time_to_tolerance(None, None, types.SimpleNamespace(width=0.8, name="fake"), None, None, 0.0, None,
+                                args)
