@@ -79,6 +79,8 @@ class Config:
     tau_max: float = 1e3
     n_org: int = 1  # Algorithm M: orthonormalise every n_org steps
     n_diag: int = 0  # Algorithm M: subspace diagonalisation every n_diag steps (0 = off)
+    tau_mode: int = 0  # 0: one Barzilai-Borwein step for all orbitals, 1: tau_i per orbital
+    solver: int = 0  # per-orbital subproblem solver: 0 steepest descent, 1 conjugate gradient
 
     @property
     def h(self):
@@ -323,6 +325,7 @@ class State:
     Z_prev: Optional[np.ndarray] = None
     tau_prev: float = 0.0
     tau_next: Optional[float] = None
+    D_prev: Optional[np.ndarray] = None  # conjugate-gradient direction of the previous step
     history: List[IterRecord] = field(default_factory=list)
     df: List[float] = field(default_factory=list)
 
@@ -355,6 +358,47 @@ def bb_step(S: np.ndarray, Y: np.ndarray, cfg: Config, l: int) -> float:
     return tau
 
 
+def bb_step_per_orbital(S: np.ndarray, Y: np.ndarray, cfg: Config, l: int) -> np.ndarray:
+    """Barzilai-Borwein step of each orbital (the tau_i of Sec. 3.2, whose
+    diagonal elements "can be done in parallel for each orbital"):
+    tau_i^1 = <s_i,s_i> / |<s_i,y_i>|, tau_i^2 = |<s_i,y_i>| / <y_i,y_i>;
+    tau_0 where a quotient is not a positive number, then clamped."""
+    N = S.shape[0]
+    dV = cfg.dV
+    ss = dV * np.sum((S * S).reshape(N, -1), axis=1)
+    sy = np.abs(dV * np.sum((S * Y).reshape(N, -1), axis=1))
+    yy = dV * np.sum((Y * Y).reshape(N, -1), axis=1)
+    variant = cfg.bb_variant
+    if variant == 3:
+        variant = 1 if (l % 2 == 0) else 2
+    with np.errstate(divide="ignore", invalid="ignore"):
+        tau = ss / sy if variant == 1 else sy / yy
+    tau = np.where(np.isfinite(tau) & (tau > 0), tau, default_tau0(cfg))
+    return np.clip(tau, cfg.tau_min, cfg.tau_max)
+
+
+def cg_direction(Z: np.ndarray, Z_prev: np.ndarray, D_prev: Optional[np.ndarray], cfg: Config) -> np.ndarray:
+    """Conjugate-gradient direction of each orbital's subproblem (Sec. 3.1
+    names CG among the solvers): d_i = z_i + beta_i d_i', with the
+    Polak-Ribiere coefficient beta_i = max(0, <z_i, z_i - z_i'> / <z_i', z_i'>)
+    (zero on the first step), capped so that <z_i, d_i> >= <z_i, z_i> / 2
+    (every orbital's direction stays a descent direction)."""
+    if D_prev is None or Z_prev is None:
+        return Z.copy()
+    N = Z.shape[0]
+    z = Z.reshape(N, -1)
+    zp = Z_prev.reshape(N, -1)
+    dp = D_prev.reshape(N, -1)
+    zz = np.sum(z * z, axis=1)
+    num = zz - np.sum(z * zp, axis=1)
+    den = np.sum(zp * zp, axis=1)
+    beta = np.where(den > 0, np.maximum(num, 0.0) / np.where(den > 0, den, 1.0), 0.0)
+    zd = np.sum(z * dp, axis=1)
+    cap = np.where(zd < 0, 0.5 * zz / np.where(zd < 0, -zd, 1.0), np.inf)
+    beta = np.minimum(beta, cap)
+    return (z + beta[:, None] * dp).reshape(Z.shape)
+
+
 def default_tau0(cfg: Config) -> float:
     return cfg.tau0 if cfg.tau0 > 0 else 1.0 / lambda_max_kinetic(cfg)
 
@@ -371,12 +415,23 @@ def search_direction(W: np.ndarray, HW: np.ndarray, cfg: Config, full: bool = Fa
 
 
 def iterate(st: State, vext: np.ndarray, cfg: Config, full_sigma: bool = False) -> State:
-    """One step l of Algorithm M (= Algorithm E when n_org = 1, n_diag = 0)."""
+    """One step l of Algorithm M (= Algorithm E when n_org = 1, n_diag = 0).
+
+    With cfg.tau_mode = 1 each orbital takes its own Barzilai-Borwein step
+    tau_i (backtracking scales them all by delta^s); with cfg.solver = 1 the
+    orbitals move along conjugate-gradient directions D instead of Z.  The
+    descent test of Eq. (ene-de) then uses the first-order decrease of the
+    step actually taken, sum_i tau_i <z_i, d_i> (= tau ||Z||_F^2 for one
+    steepest-descent step).
+    """
     W = st.W
     HW = apply_h(W, st.V, cfg)
     Z, sigma = search_direction(W, HW, cfg, full=full_sigma)
     dV = cfg.dV
-    znorm2 = dV * float(np.sum(Z * Z))
+    N = W.shape[0]
+    D = cg_direction(Z, st.Z_prev, st.D_prev, cfg) if cfg.solver == 1 else Z
+    zd = dV * np.sum((Z * D).reshape(N, -1), axis=1)  # <z_i, d_i>
+    znorm2 = float(np.sum(zd))
     tau0 = default_tau0(cfg)
     if st.tau_next is not None:
         tau = st.tau_next  # computed before a subspace rotation (see subspace_diagonalise)
@@ -388,27 +443,32 @@ def iterate(st: State, vext: np.ndarray, cfg: Config, full_sigma: bool = False) 
     if not math.isfinite(tau) or tau <= 0:
         tau = tau0
     tau = min(max(tau, cfg.tau_min), cfg.tau_max)
+    # relative per-orbital steps: tau_i = tau * fac_i
+    fac = np.ones(N)
+    if cfg.tau_mode == 1 and st.W_prev is not None:
+        fac = bb_step_per_orbital(W - st.W_prev, Z - st.Z_prev, cfg, st.l) / tau
 
     orth_step = (st.l % max(cfg.n_org, 1)) == 0
     if not orth_step:
         # Algorithm M, intermediate step: plain update, no Orth, no backtracking
-        Wn = W - tau * Z
+        Wn = W - tau * fac[:, None, None, None] * D
         rho = density(Wn)
         V = total_potential(rho, vext, cfg)
-        st.W_prev, st.Z_prev = W, Z
+        st.W_prev, st.Z_prev, st.D_prev = W, Z, D
         st.W, st.rho, st.V = Wn, rho, V
         st.l += 1
         st.history.append(IterRecord(float("nan"), tau, 0, False, float("nan"), znorm2))
         return st
+    decrease = float(np.sum(fac * zd))  # sum_i fac_i <z_i, d_i>
 
     backtracks = 0
     forced = False
     while True:
         t = tau * cfg.delta ** backtracks
-        Wt = W - t * Z
+        Wt = W - t * fac[:, None, None, None] * D
         Wn, Sg, _ = cholesky_qr(Wt, cfg)
         En = energy(Wn, vext, cfg)
-        if En <= st.C - cfg.rho1 * t * znorm2:
+        if En <= st.C - cfg.rho1 * t * decrease:
             break
         if backtracks >= cfg.max_backtrack:
             forced = True
@@ -419,7 +479,7 @@ def iterate(st: State, vext: np.ndarray, cfg: Config, full_sigma: bool = False) 
     Cn = (cfg.eta * st.Q * st.C + En) / Qn
     rho = density(Wn)
     V = total_potential(rho, vext, cfg)
-    st.W_prev, st.Z_prev = W, Z
+    st.W_prev, st.Z_prev, st.D_prev = W, Z, D
     E_old = st.E
     st.W, st.rho, st.V, st.E, st.C, st.Q = Wn, rho, V, En, Cn, Qn
     st.tau_prev = t
@@ -449,6 +509,7 @@ def subspace_diagonalise(st: State, vext: np.ndarray, cfg: Config, full_sigma: b
     st.W = (P.T @ W.reshape(N, -1)).reshape(W.shape)
     st.W_prev = None
     st.Z_prev = None
+    st.D_prev = None
 
 
 def converged_df(df: List[float], e_tol: float) -> bool:
