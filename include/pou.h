@@ -101,6 +101,16 @@ typedef struct {
                          1 OptM-QR, the comparison method of Table 1, Z = HW - W Sigma with the full
                          Sigma = <W^T H W>, its own Barzilai-Borwein differences Y = Z - Z'.  1 needs
                          n_org = 1 and n_diag = 0, and two more orbital blocks of device memory */
+  int tau_mode;       /* 0 (default): one Barzilai-Borwein step for all orbitals; 1: a step tau_i per
+                         orbital from its own s_i, y_i (Sec. 3.2's tau_i); backtracking scales all by
+                         delta^s and Eq. ene-de takes sum_i tau_i ||z_i||^2.  1 needs direction = 0,
+                         solver = 0, n_org = 1, n_diag = 0 */
+  int solver;         /* per-orbital subproblem solver (Sec. 3.1): 0 (default) steepest descent;
+                         1 conjugate gradient: d_i = z_i + beta_i (d_i' - <w_i,d_i'> w_i), Polak-Ribiere
+                         beta_i >= 0 capped so that <z_i,d_i> >= <z_i,z_i>/2, and the Newton step
+                         tau_i = <z_i,d_i> / <d_i,(H - sigma_ii) d_i> of each orbital's frozen-potential
+                         Rayleigh quotient; Eq. ene-de takes sum_i tau_i <z_i,d_i>.  1 needs direction = 0,
+                         tau_mode = 0, n_org = 1, n_diag = 0, and four more orbital blocks */
 } pou_config;
 
 #define POU_MAX_N 512      /* FP32 form (without the subspace diagonalisation) */

@@ -377,26 +377,50 @@ def bb_step_per_orbital(S: np.ndarray, Y: np.ndarray, cfg: Config, l: int) -> np
     return np.clip(tau, cfg.tau_min, cfg.tau_max)
 
 
-def cg_direction(Z: np.ndarray, Z_prev: np.ndarray, D_prev: Optional[np.ndarray], cfg: Config) -> np.ndarray:
+def cg_direction(W: np.ndarray, Z: np.ndarray, Z_prev: Optional[np.ndarray], D_prev: Optional[np.ndarray],
+                 cfg: Config) -> np.ndarray:
     """Conjugate-gradient direction of each orbital's subproblem (Sec. 3.1
-    names CG among the solvers): d_i = z_i + beta_i d_i', with the
-    Polak-Ribiere coefficient beta_i = max(0, <z_i, z_i - z_i'> / <z_i', z_i'>)
-    (zero on the first step), capped so that <z_i, d_i> >= <z_i, z_i> / 2
-    (every orbital's direction stays a descent direction)."""
+    names conjugate gradients among the solvers): d_i = z_i + beta_i d_i'',
+    d_i'' = d_i' - <w_i, d_i'> w_i (the previous direction without its w_i
+    component), with the Polak-Ribiere coefficient
+    beta_i = max(0, <z_i, z_i - z_i'>) / <z_i', z_i'> (zero on the first step),
+    capped so that <z_i, d_i> >= <z_i, z_i> / 2 (every orbital keeps a descent
+    direction)."""
     if D_prev is None or Z_prev is None:
         return Z.copy()
     N = Z.shape[0]
+    w = W.reshape(N, -1)
     z = Z.reshape(N, -1)
     zp = Z_prev.reshape(N, -1)
     dp = D_prev.reshape(N, -1)
+    gamma = cfg.dV * np.sum(w * dp, axis=1)
+    dpp = dp - gamma[:, None] * w
     zz = np.sum(z * z, axis=1)
-    num = zz - np.sum(z * zp, axis=1)
     den = np.sum(zp * zp, axis=1)
-    beta = np.where(den > 0, np.maximum(num, 0.0) / np.where(den > 0, den, 1.0), 0.0)
-    zd = np.sum(z * dp, axis=1)
+    beta = np.where(den > 0, np.maximum(zz - np.sum(z * zp, axis=1), 0.0) / np.where(den > 0, den, 1.0), 0.0)
+    zd = np.sum(z * dpp, axis=1)
     cap = np.where(zd < 0, 0.5 * zz / np.where(zd < 0, -zd, 1.0), np.inf)
     beta = np.minimum(beta, cap)
-    return (z + beta[:, None] * dp).reshape(Z.shape)
+    return (z + beta[:, None] * dpp).reshape(Z.shape)
+
+
+def newton_steps(D: np.ndarray, Z: np.ndarray, V: np.ndarray, sigma: np.ndarray, cfg: Config) -> np.ndarray:
+    """Per-orbital Newton step along d_i of the Rayleigh quotient of orbital i
+    with the potential frozen: for a tangent direction d_i (<w_i, d_i> = 0)
+    the quotient at w_i - t d_i is sigma_ii - 2 t <z_i, d_i> +
+    t^2 <d_i, (H - sigma_ii) d_i> to second order, minimised at
+    t_i = <z_i, d_i> / <d_i, (H - sigma_ii) d_i>; tau_0 where that is not a
+    positive number; clamped."""
+    N = D.shape[0]
+    dV = cfg.dV
+    HD = apply_h(D, V, cfg)
+    d = D.reshape(N, -1)
+    zd = dV * np.sum(Z.reshape(N, -1) * d, axis=1)
+    den = dV * (np.sum(d * HD.reshape(N, -1), axis=1) - sigma * np.sum(d * d, axis=1))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t = np.where((den > 0) & (zd > 0), zd / den, default_tau0(cfg))
+    t = np.where(np.isfinite(t) & (t > 0), t, default_tau0(cfg))
+    return np.clip(t, cfg.tau_min, cfg.tau_max)
 
 
 def default_tau0(cfg: Config) -> float:
@@ -419,9 +443,10 @@ def iterate(st: State, vext: np.ndarray, cfg: Config, full_sigma: bool = False) 
 
     With cfg.tau_mode = 1 each orbital takes its own Barzilai-Borwein step
     tau_i (backtracking scales them all by delta^s); with cfg.solver = 1 the
-    orbitals move along conjugate-gradient directions D instead of Z.  The
-    descent test of Eq. (ene-de) then uses the first-order decrease of the
-    step actually taken, sum_i tau_i <z_i, d_i> (= tau ||Z||_F^2 for one
+    orbitals move along conjugate-gradient directions D instead of Z, each
+    with its Newton step (``newton_steps``; tau is their mean).  The descent
+    test of Eq. (ene-de) then uses the first-order decrease of the step
+    actually taken, sum_i tau_i <z_i, d_i> (= tau ||Z||_F^2 for one
     steepest-descent step).
     """
     W = st.W
@@ -429,7 +454,7 @@ def iterate(st: State, vext: np.ndarray, cfg: Config, full_sigma: bool = False) 
     Z, sigma = search_direction(W, HW, cfg, full=full_sigma)
     dV = cfg.dV
     N = W.shape[0]
-    D = cg_direction(Z, st.Z_prev, st.D_prev, cfg) if cfg.solver == 1 else Z
+    D = cg_direction(W, Z, st.Z_prev, st.D_prev, cfg) if cfg.solver == 1 else Z
     zd = dV * np.sum((Z * D).reshape(N, -1), axis=1)  # <z_i, d_i>
     znorm2 = float(np.sum(zd))
     tau0 = default_tau0(cfg)
@@ -445,7 +470,12 @@ def iterate(st: State, vext: np.ndarray, cfg: Config, full_sigma: bool = False) 
     tau = min(max(tau, cfg.tau_min), cfg.tau_max)
     # relative per-orbital steps: tau_i = tau * fac_i
     fac = np.ones(N)
-    if cfg.tau_mode == 1 and st.W_prev is not None:
+    if cfg.solver == 1:
+        # conjugate gradients: each orbital's Newton step; tau is their mean
+        tsteps = newton_steps(D, Z, st.V, sigma, cfg)
+        tau = float(np.mean(tsteps))
+        fac = tsteps / tau
+    elif cfg.tau_mode == 1 and st.W_prev is not None:
         fac = bb_step_per_orbital(W - st.W_prev, Z - st.Z_prev, cfg, st.l) / tau
 
     orth_step = (st.l % max(cfg.n_org, 1)) == 0

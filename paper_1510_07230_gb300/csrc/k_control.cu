@@ -137,6 +137,8 @@ __global__ void __launch_bounds__(KNT) k_control(CtrlArgs a) {
     st->diag_count = 0;
     st->orth_now = 1;
     st->done = 1;
+    if (a.tfac)
+      for (int i = 0; i < N; ++i) a.tfac[i] = 1.0;  // first step: tau_0 for every orbital
     return;
   }
   st->passes += 1;
@@ -185,6 +187,26 @@ __global__ void __launch_bounds__(KNT) k_control(CtrlArgs a) {
   st->tau_bb = tau;
   st->tau_trial = tau;
   st->s = 0;
+  if (a.tfac) {
+    // per-orbital steps (the tau_i of Sec. 3.2): the same quotient from the
+    // orbital's own s_i, y_i, kept as a factor on the common tau; the
+    // Eq. (ene-de) decrease becomes sum_i tau_i ||z_i||^2 = tau * znorm2
+    double zf = 0.0;
+    for (int i = 0; i < N; ++i) {
+      const double* p = part + i * NP;
+      const double ds = a.sigma[t][i] - p[P_SIGP];
+      const double ssi = p[P_SS];
+      const double syi = fabs(p[P_SB] - ds * p[P_SW]);
+      const double yyi = p[P_BB] - 2.0 * ds * p[P_BW] + ds * ds * p[P_WW];
+      double ti = (variant == 1) ? (syi > 0.0 ? ssi / syi : NAN) : (yyi > 0.0 ? syi / yyi : NAN);
+      if (!isfinite(ti) || ti <= 0.0) ti = a.tau0;
+      ti = fmin(fmax(ti, a.tau_min), a.tau_max);
+      const double fi = ti / tau;
+      a.tfac[i] = fi;
+      zf += fi * (p[P_ZZ] - 2.0 * ds * p[P_ZW] + ds * ds * p[P_WW]);
+    }
+    st->znorm2 = zf * dV;
+  }
   // Algorithm M: subspace diagonalisation every n_diag steps (after an
   // orthonormalised step), before the next trial; Orth every n_org steps
   st->diag_now = (orth && a.n_diag > 0 && st->l % a.n_diag == 0) ? 1 : 0;

@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(GNT, 1) k_gram(GramArgs<T> a, i64 ntiles, int 
   constexpr int PER = ST * BK / GNT;  // tile elements loaded per thread
   __shared__ __align__(16) T As[2][BK][ST + 4];
   __shared__ __align__(16) T Bs[2][BK][ST + 4];
-  __shared__ T coefs[ST], coefs2[ST];
+  __shared__ T coefs[ST], coefs2[ST], taus[ST], taus2[ST];
 
   if (a.st && a.st->done) return;
   if (!gate_open(a.st, a.gate)) return;
@@ -93,18 +93,20 @@ __global__ void __launch_bounds__(GNT, 1) k_gram(GramArgs<T> a, i64 ntiles, int 
   const T* Wa;
   const T* Ha = nullptr;
   const T* Bsrc;
-  T tauT = T(0);
   if (a.trial) {
     const int cur = a.st->cur;
     Wa = a.W[cur];
     Ha = a.HW[cur];
     Bsrc = Wa;
     const double tau = a.st->tau_trial;
-    tauT = (T)tau;
     for (int r = tid; r < ST; r += GNT) {
       const int gi = I * ST + r, gj = J * ST + r;
-      coefs[r] = gi < N ? (T)(1.0 + tau * a.sigma[cur][gi]) : T(0);
-      coefs2[r] = gj < N ? (T)(1.0 + tau * a.sigma[cur][gj]) : T(0);
+      const double ti = (gi < N && a.tfac) ? tau * a.tfac[gi] : tau;
+      const double tj = (gj < N && a.tfac) ? tau * a.tfac[gj] : tau;
+      coefs[r] = gi < N ? (T)(1.0 + ti * a.sigma[cur][gi]) : T(0);
+      coefs2[r] = gj < N ? (T)(1.0 + tj * a.sigma[cur][gj]) : T(0);
+      taus[r] = (T)ti;
+      taus2[r] = (T)tj;
     }
   } else if (a.src_trial_slot) {
     Wa = a.W[1 - a.st->cur];
@@ -142,8 +144,8 @@ __global__ void __launch_bounds__(GNT, 1) k_gram(GramArgs<T> a, i64 ntiles, int 
     for (int q = 0; q < PER; ++q) {
       const int e = tid + q * GNT;
       const int r = e / BK, k = e % BK;
-      As[buf][k][r] = a.trial ? coefs[r] * pa[q] - tauT * pah[q] : pa[q];
-      if (!diag) Bs[buf][k][r] = a.trial ? coefs2[r] * pb[q] - tauT * pbh[q] : pb[q];
+      As[buf][k][r] = a.trial ? coefs[r] * pa[q] - taus[r] * pah[q] : pa[q];
+      if (!diag) Bs[buf][k][r] = a.trial ? coefs2[r] * pb[q] - taus2[r] * pbh[q] : pb[q];
     }
   };
 
@@ -228,9 +230,10 @@ __global__ void k_gram_reduce(GramReduceArgs a) {
   }
   s *= a.dV;
   if (a.trial == 2 && r == c) {
-    // OptM-QR: the trial column w - tau z, z the direction block; FP64 sums
-    // of the kernel that formed z
-    const double tau = a.st->tau_trial;
+    // a materialised direction (OptM-QR, conjugate gradient): the trial
+    // column w - t z, z the direction block; FP64 sums of the kernel that
+    // formed z
+    const double tau = a.st->tau_trial * (a.tfac ? a.tfac[r] : 1.0);
     const double* dp = a.dpart + (i64)r * 3;
     s = a.dV * (dp[0] - 2.0 * tau * dp[1] + tau * tau * dp[2]);
   } else if (a.trial && r == c) {
@@ -240,7 +243,7 @@ __global__ void k_gram_reduce(GramReduceArgs a) {
     //   z_e = z' - d w with z' = hw - sigma' w, d = s_e - sigma',
     //   ||w - t z_e||^2 = <w,w> - 2 t <w,z_e> + t^2 <z_e,z_e>.
     const int cur = a.st->cur;
-    const double tau = a.st->tau_trial;
+    const double tau = a.st->tau_trial * (a.tfac ? a.tfac[r] : 1.0);
     const double coef = 1.0 + tau * a.sigma[cur][r];
     const double t = tau;
     const double* pp = a.part[cur] + (i64)r * NP;
@@ -269,6 +272,7 @@ __global__ void __launch_bounds__(RNT) k_rotate(RotArgs<double> a, int nchunks) 
   double* Rs = reinterpret_cast<double*>(smem_raw);  // [NPAD][NPAD]
   double* Xs = Rs + NPAD * NPAD;                      // [NPAD][RP + 4]
   double* coefs = Xs + NPAD * (RP + 4);               // [NPAD]
+  double* taus = coefs + NPAD;                        // [NPAD] per-orbital trial step
   constexpr int XS = RP + 4;
 
   if (a.st && a.st->done) return;
@@ -286,7 +290,11 @@ __global__ void __launch_bounds__(RNT) k_rotate(RotArgs<double> a, int nchunks) 
     out = a.Wout[1 - cur];
     rho = a.rho[1 - cur];
     tau = a.st->tau_trial;
-    for (int i = tid; i < NPAD; i += RNT) coefs[i] = i < N ? 1.0 + tau * a.sigma[cur][i] : 0.0;
+    for (int i = tid; i < NPAD; i += RNT) {
+      const double t = (i < N && a.tfac) ? tau * a.tfac[i] : tau;
+      coefs[i] = i < N ? 1.0 + t * a.sigma[cur][i] : 0.0;
+      taus[i] = t;
+    }
   } else if (a.st) {
     const int cur = a.st->cur;
     // in-place passes read the block they overwrite: every chunk is staged in
@@ -327,7 +335,7 @@ __global__ void __launch_bounds__(RNT) k_rotate(RotArgs<double> a, int nchunks) 
       double v = 0.0;
       if (gp < ng) {
         const i64 off = (i64)i * ng + gp;
-        v = a.trial ? coefs[i] * Wsrc[off] - tau * Hsrc[off] : Wsrc[off];
+        v = a.trial ? coefs[i] * Wsrc[off] - taus[i] * Hsrc[off] : Wsrc[off];
       }
       Xs[i * XS + pp] = v;
     }
@@ -748,7 +756,7 @@ void launch_gram_reduce(const GramReduceArgs& a, cudaStream_t s) {
 
 static size_t rotate_smem() {
   const int NPAD = 128;
-  return sizeof(double) * ((size_t)NPAD * NPAD + (size_t)NPAD * (RP + 4) + NPAD);
+  return sizeof(double) * ((size_t)NPAD * NPAD + (size_t)NPAD * (RP + 4) + 2 * NPAD);
 }
 static size_t rotate_f32_smem() {
   const int NPAD = 128;

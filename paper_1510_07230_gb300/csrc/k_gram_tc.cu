@@ -69,9 +69,10 @@ constexpr int OFF_BAR = OFF_DIAG + 128 * 8;
 // barriers: full[STAGES], empty[STAGES], accf[2], acce[2], fin; then tmem slot, abort flag, coefs
 constexpr int NBAR = 2 * STAGES + 5;
 constexpr int OFF_MISC = OFF_BAR + NBAR * 8;
-constexpr int OFF_COEF = OFF_MISC + 16;
+constexpr int OFF_COEF = (OFF_MISC + 16 + 15) / 16 * 16;  // float4 entries: 16-byte aligned
+static_assert(OFF_COEF % 16 == 0, "coefficient entries must be 16-byte aligned");
 constexpr int MAXN = 512;            // orbitals: at most four 128-row blocks
-constexpr int SMEM_BYTES = OFF_COEF + MAXN * 8 + 1024;  // + alignment slack
+constexpr int SMEM_BYTES = OFF_COEF + MAXN * 16 + 1024;  // + alignment slack
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t COL_SUM = 256, COL_ERR = 384;
 constexpr uint32_t IDESC = tc::idesc_tf32(128, 128);
@@ -112,7 +113,8 @@ __global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb)
   const uint32_t fin_bar = bar0 + 8u * (2 * STAGES + 4);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + OFF_MISC);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + OFF_MISC + 4);
-  float2* coefs = reinterpret_cast<float2*>(smem + OFF_COEF);  // 1 + tau sigma_i as (hi, lo)
+  // per orbital: 1 + t_i sigma_i and its step t_i, each as (hi, lo)
+  float4* coefs = reinterpret_cast<float4*>(smem + OFF_COEF);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int N = a.N;
@@ -136,18 +138,16 @@ __global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb)
 
   const float* Wa;
   const float* Ha = nullptr;
-  float tauH = 0.f, tauL = 0.f;
   if (TRIAL) {
     const int cur = a.st->cur;
     Wa = a.W[cur];
     Ha = a.HW[cur];
     const double tau = a.st->tau_trial;
-    tauH = (float)tau;
-    tauL = (float)(tau - (double)tauH);
     for (int r = tid; r < MAXN; r += NTHR) {
-      const double cf = r < N ? 1.0 + tau * a.sigma[cur][r] : 0.0;
-      const float ch = (float)cf;
-      coefs[r] = make_float2(ch, (float)(cf - (double)ch));
+      const double t = (r < N && a.tfac) ? tau * a.tfac[r] : tau;
+      const double cf = r < N ? 1.0 + t * a.sigma[cur][r] : 0.0;
+      const float ch = (float)cf, th = (float)t;
+      coefs[r] = make_float4(ch, (float)(cf - (double)ch), th, (float)(t - (double)th));
     }
   } else if (a.src_trial_slot) {
     Wa = a.W[1 - a.st->cur];
@@ -232,11 +232,11 @@ __global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb)
         const float x[4] = {w[q].x, w[q].y, w[q].z, w[q].w};
         float hi[4], lo[4];
         if (TRIAL) {
-          const float2 cf = coefs[rb + r];
+          const float4 cf = coefs[rb + r];
           const float hv4[4] = {h[q].x, h[q].y, h[q].z, h[q].w};
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            tc::trial_split(cf.x, cf.y, x[e], tauH, tauL, hv4[e], hi[e], lo[e]);
+            tc::trial_split(cf.x, cf.y, x[e], cf.z, cf.w, hv4[e], hi[e], lo[e]);
             lo[e] *= lo_scale;
           }
         } else {

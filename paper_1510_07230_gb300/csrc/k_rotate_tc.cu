@@ -74,8 +74,9 @@ constexpr int OFF_RHI = 0;
 constexpr int OFF_RLO = OFF_RHI + R_BYTES;
 constexpr int OFF_X = OFF_RLO + R_BYTES;           // four X atom slots (one tile)
 constexpr int OFF_SELF = OFF_X + 4 * SLOT;         // 128 x float2: R_jj as (hi, lo)
-constexpr int OFF_COEF = OFF_SELF + 128 * 8;       // 128 x float2: 1 + tau sigma_i as (hi, lo)
-constexpr int OFF_DENS = OFF_COEF + 128 * 8;       // [4 quadrants][32] x (s, c)
+constexpr int OFF_COEF = OFF_SELF + 128 * 8;       // 128 x float4: 1 + t_i sigma_i, t_i as (hi, lo)
+constexpr int OFF_DENS = OFF_COEF + 128 * 16;      // [4 quadrants][32] x (s, c)
+static_assert(OFF_COEF % 16 == 0, "coefficient entries must be 16-byte aligned");
 constexpr int OFF_BAR = OFF_DENS + 4 * 32 * 8;
 // barriers: full[4], empty[4], accf, acce, fin; then tmem slot, abort flag
 constexpr int NBAR = 11;
@@ -130,7 +131,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_rotate_tc(RotArgs<float> a, i64 nti
   const uint32_t sbase = raw_addr + pad;
   float2* self = reinterpret_cast<float2*>(smem + OFF_SELF);  // R_jj as (hi, lo)
   float2* dens = reinterpret_cast<float2*>(smem + OFF_DENS);
-  float2* coefs = reinterpret_cast<float2*>(smem + OFF_COEF);
+  float4* coefs = reinterpret_cast<float4*>(smem + OFF_COEF);
   const uint32_t bar0 = sbase + OFF_BAR;
   auto full_bar = [&](int k) { return bar0 + 8u * k; };
   auto empty_bar = [&](int k) { return bar0 + 8u * (4 + k); };
@@ -172,7 +173,6 @@ __global__ void __launch_bounds__(NTHR, 1) k_rotate_tc(RotArgs<float> a, i64 nti
     out = a.B;
     rho = a.rho_out;
   }
-  const float tauH = (float)tau, tauL = (float)(tau - (double)tauH);
 
   // B operand = strictly upper R (row j, K index i) split into TF32 pairs,
   // rows j >= 32 k of atom k only; the self-term coefficients R_jj; the
@@ -191,14 +191,15 @@ __global__ void __launch_bounds__(NTHR, 1) k_rotate_tc(RotArgs<float> a, i64 nti
     *reinterpret_cast<float*>(smem + OFF_RLO + off) = lo;
   }
   for (int j = tid; j < 128; j += NTHR) {
-    double A = 0.0, cf = 1.0;
+    double A = 0.0, cf = 1.0, t = tau;
     if (j < N) {
       A = a.Rinv[(i64)j * N + j];
-      if (a.trial) cf = 1.0 + tau * a.sigma[cur][j];
+      if (a.trial && a.tfac) t = tau * a.tfac[j];
+      if (a.trial) cf = 1.0 + t * a.sigma[cur][j];
     }
-    const float ah = (float)A, ch = (float)cf;
+    const float ah = (float)A, ch = (float)cf, th = (float)t;
     self[j] = make_float2(ah, (float)(A - (double)ah));
-    coefs[j] = make_float2(ch, (float)(cf - (double)ch));
+    coefs[j] = make_float4(ch, (float)(cf - (double)ch), th, (float)(t - (double)th));
   }
   if (tid == 0) {
     for (int k = 0; k < 4; ++k) {
@@ -275,7 +276,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_rotate_tc(RotArgs<float> a, i64 nti
       // the previous tile's MMAs and epilogue are done with the slot
       if (t > 0 && !tc::mbar_wait(empty_bar(k), (t - 1) & 1, abort_flag)) return false;
       unsigned char* xs = smem + OFF_X + k * SLOT;
-      const float2 cf = coefs[32 * k + 4 * warp + isub];
+      const float4 cf = coefs[32 * k + 4 * warp + isub];
 #pragma unroll
       for (int g = 0; g < 4; ++g) {
         const float x[4] = {w[g].x, w[g].y, w[g].z, w[g].w};
@@ -285,7 +286,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_rotate_tc(RotArgs<float> a, i64 nti
           const int row = 32 * g + 8 * e + q;  // holds point 32 g + 4 q + e; row % 8 == q
           float hi, lo;
           if (Hsrc) {
-            tc::trial_split(cf.x, cf.y, x[e], tauH, tauL, h4[e], hi, lo);
+            tc::trial_split(cf.x, cf.y, x[e], cf.z, cf.w, h4[e], hi, lo);
           } else {
             hi = tc::to_tf32(x[e]);
             lo = x[e] - hi;  // exact
@@ -482,8 +483,9 @@ constexpr int BIG_MAXN = 512;
 constexpr int B_OFF_R = 0;                             // two R atom slots (hi rows, then lo rows)
 constexpr int B_OFF_X = 2 * SLOT;                      // four X atom slots
 constexpr int B_OFF_SELF = B_OFF_X + 4 * SLOT;         // BIG_MAXN x float2: R_jj (hi, lo)
-constexpr int B_OFF_COEF = B_OFF_SELF + BIG_MAXN * 8;  // BIG_MAXN x float2: 1 + tau sigma_i
-constexpr int B_OFF_DENS = B_OFF_COEF + BIG_MAXN * 8;
+constexpr int B_OFF_COEF = B_OFF_SELF + BIG_MAXN * 8;  // BIG_MAXN x float4: 1 + t_i sigma_i, t_i
+constexpr int B_OFF_DENS = B_OFF_COEF + BIG_MAXN * 16;
+static_assert(B_OFF_COEF % 16 == 0, "coefficient entries must be 16-byte aligned");
 constexpr int B_OFF_BAR = B_OFF_DENS + 4 * 32 * 8;
 // barriers: fullx[4], emptyx[4], xfree[4], fullr[2], emptyr[2], accf, acce, fin
 constexpr int B_NBAR = 19;
@@ -527,7 +529,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_rotate_tc_big(RotArgs<float> a, i64
   unsigned char* smem = smem_raw + pad;
   const uint32_t sbase = raw_addr + pad;
   float2* self = reinterpret_cast<float2*>(smem + B_OFF_SELF);
-  float2* coefs = reinterpret_cast<float2*>(smem + B_OFF_COEF);
+  float4* coefs = reinterpret_cast<float4*>(smem + B_OFF_COEF);
   float2* dens = reinterpret_cast<float2*>(smem + B_OFF_DENS);
   const uint32_t bar0 = sbase + B_OFF_BAR;
   auto fullx = [&](int k) { return bar0 + 8u * k; };
@@ -567,18 +569,18 @@ __global__ void __launch_bounds__(NTHR, 1) k_rotate_tc_big(RotArgs<float> a, i64
     out = a.B;
     rho = a.rho_out;
   }
-  const float tauH = (float)tau, tauL = (float)(tau - (double)tauH);
   const unsigned char* img = reinterpret_cast<const unsigned char*>(a.rimg);
 
   for (int j = tid; j < BIG_MAXN; j += NTHR) {
-    double A = 0.0, cf = 1.0;
+    double A = 0.0, cf = 1.0, t = tau;
     if (j < N) {
       A = a.Rinv[(i64)j * N + j];
-      if (a.trial) cf = 1.0 + tau * a.sigma[cur][j];
+      if (a.trial && a.tfac) t = tau * a.tfac[j];
+      if (a.trial) cf = 1.0 + t * a.sigma[cur][j];
     }
-    const float ah = (float)A, ch = (float)cf;
+    const float ah = (float)A, ch = (float)cf, th = (float)t;
     self[j] = make_float2(ah, (float)(A - (double)ah));
-    coefs[j] = make_float2(ch, (float)(cf - (double)ch));
+    coefs[j] = make_float4(ch, (float)(cf - (double)ch), th, (float)(t - (double)th));
   }
   if (tid == 0) {
     for (int k = 0; k < 4; ++k) {
@@ -678,7 +680,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_rotate_tc_big(RotArgs<float> a, i64
       if (u >= 4 && !tc::mbar_wait(emptyx(slot), ((u >> 2) - 1) & 1, abort_flag)) return false;
       if (k < 4 && P > 0 && !tc::mbar_wait(xfree(slot), (P - 1) & 1, abort_flag)) return false;
       unsigned char* xs = smem + B_OFF_X + slot * SLOT;
-      const float2 cf = coefs[min(32 * k + 4 * warp + isub, BIG_MAXN - 1)];
+      const float4 cf = coefs[min(32 * k + 4 * warp + isub, BIG_MAXN - 1)];
 #pragma unroll
       for (int g = 0; g < 4; ++g) {
         const float x[4] = {w[g].x, w[g].y, w[g].z, w[g].w};
@@ -688,7 +690,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_rotate_tc_big(RotArgs<float> a, i64
           const int row = 32 * g + 8 * e + q;
           float hi, lo;
           if (Hsrc) {
-            tc::trial_split(cf.x, cf.y, x[e], tauH, tauL, h4[e], hi, lo);
+            tc::trial_split(cf.x, cf.y, x[e], cf.z, cf.w, h4[e], hi, lo);
           } else {
             hi = tc::to_tf32(x[e]);
             lo = x[e] - hi;

@@ -100,8 +100,9 @@ __global__ void __launch_bounds__(NT) k_apply_h(ApplyArgs<T> a) {
 
   if (a.st && a.st->done) return;
   if (a.mode == 3 && !a.st->diag_now) return;
+  if (a.mode == 4 && a.st->s != 0) return;
   const int cur = a.st ? a.st->cur : 0;
-  const int t = (a.mode == 2) ? 0 : (a.mode == 3 ? cur : 1 - cur);
+  const int t = (a.mode == 2) ? 0 : ((a.mode == 3 || a.mode == 4) ? cur : 1 - cur);
   const bool prev = (a.mode == 0);
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const i64 ng = (i64)nx * ny * nz;
@@ -339,8 +340,9 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_apply_h_pair(App
 
   if (a.st && a.st->done) return;
   if (a.mode == 3 && !a.st->diag_now) return;
+  if (a.mode == 4 && a.st->s != 0) return;
   const int cur = a.st ? a.st->cur : 0;
-  const int t = (a.mode == 2) ? 0 : (a.mode == 3 ? cur : 1 - cur);
+  const int t = (a.mode == 2) ? 0 : ((a.mode == 3 || a.mode == 4) ? cur : 1 - cur);
   const bool prev = (a.mode == 0);
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const i64 pl = (i64)nx * ny;
@@ -693,8 +695,9 @@ __global__ void __launch_bounds__(NTP, CUBIC ? 3 : 2) k_apply_h_pk(ApplyArgs<flo
 
   if (a.st && a.st->done) return;
   if (a.mode == 3 && !a.st->diag_now) return;
+  if (a.mode == 4 && a.st->s != 0) return;
   const int cur = a.st ? a.st->cur : 0;
-  const int t = (a.mode == 2) ? 0 : (a.mode == 3 ? cur : 1 - cur);
+  const int t = (a.mode == 2) ? 0 : ((a.mode == 3 || a.mode == 4) ? cur : 1 - cur);
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const i64 pl = (i64)nx * ny;
   const i64 ng = pl * nz;

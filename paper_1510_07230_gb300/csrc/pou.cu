@@ -127,6 +127,14 @@ struct pou_ctx {
   double* dir_bpart;
   double* dir_dpart;
   double* zero_sigma;
+  // per-orbital step factors (tau_mode = 1, solver = 1); conjugate-gradient
+  // directions and the z of the previous step, their partial sums and
+  // coefficients (solver = 1)
+  double* tfac;
+  void* D[2];
+  void* Zs[2];
+  double* cg_opart;
+  double* cg_coef;
   State* st;
   double* hist_E;
   double* hist_tau;
@@ -443,12 +451,79 @@ void enqueue_direction_full(pou_ctx* c) {
   launch_direction_control(k, s);
 }
 
+// Conjugate-gradient solver: on the first pass of a step, the directions D,
+// the H-apply of D for the Newton steps, and the per-orbital steps.
+template <typename T>
+void enqueue_cg(pou_ctx* c) {
+  cudaStream_t s = c->stream;
+  CgArgs<T> g{};
+  g.st = c->st;
+  for (int k = 0; k < 2; ++k) {
+    g.W[k] = tp<T>(c->W[k]);
+    g.HW[k] = tp<T>(c->HW[k]);
+    g.D[k] = tp<T>(c->D[k]);
+    g.Zs[k] = tp<T>(c->Zs[k]);
+    g.sigma[k] = c->sigma[k];
+  }
+  g.coef = c->cg_coef;
+  g.opart = c->cg_opart;
+  g.ng = c->ng;
+  g.N = c->N;
+  g.nch = cg_chunks(c->ng);
+  CgCtrlArgs k{};
+  k.st = c->st;
+  k.opart = c->cg_opart;
+  k.nch = g.nch;
+  k.N = c->N;
+  k.coef = c->cg_coef;
+  for (int q = 0; q < 2; ++q) k.sigma[q] = c->sigma[q];
+  k.tilepart = c->tilepart;
+  k.tfac = c->tfac;
+  k.dpart = c->dir_dpart;
+  k.dV = c->dV;
+  k.tau0 = c->tau0;
+  k.tau_min = c->cfg.tau_min;
+  k.tau_max = c->cfg.tau_max;
+  launch_cg_dots<T>(g, s);
+  launch_cg_beta(k, s);
+  launch_cg_form<T>(g, s);
+  ApplyArgs<T> aa{};
+  aa.st = c->st;
+  for (int q = 0; q < 2; ++q) {
+    aa.W[q] = tp<T>(c->D[q]);
+    aa.HW[q] = nullptr;
+    aa.V[q] = tp<T>(c->V[q]);
+    aa.sigma[q] = c->sigma[q];
+  }
+  aa.mode = 4;
+  aa.tilepart = c->tilepart;
+  aa.out_scale = T(1);
+  aa.N = c->N;
+  aa.nx = c->nx;
+  aa.ny = c->ny;
+  aa.nz = c->nz;
+  aa.ihx2 = (T)stencil_scale(c, 0);
+  aa.ihy2 = (T)stencil_scale(c, 1);
+  aa.ihz2 = (T)stencil_scale(c, 2);
+  aa.cubic = cubic_scales(c);
+  int ntile = 0;
+  launch_apply_h<T>(aa, c->cfg.stencil_order, s, &ntile);
+  k.ntile = ntile;
+  launch_cg_step(k, s);
+}
+
 template <typename T>
 void enqueue_pass(pou_ctx* c) {
   cudaStream_t s = c->stream;
   if (c->cfg.n_diag > 0) enqueue_diag<T>(c);
   const bool full = c->cfg.direction == 1;
+  const bool cg = c->cfg.solver == 1;
   if (full) enqueue_direction_full<T>(c);
+  if (cg) enqueue_cg<T>(c);
+  // the trial kernels take a materialised direction (OptM-QR's Z, the CG
+  // directions D) with a zero sigma, or Opt-Par's (W, HW, sigma)
+  void* const* dirb = full ? c->Z : (cg ? c->D : c->HW);
+  const bool mat = full || cg;
   // trial block Wt = W - tau Z from the current pair, Gram matrix
   // the trial point (1 + tau sigma_ii) w - tau hw of Opt-Par; OptM-QR hands
   // the kernels Z and a zero sigma, so that they form w - tau z
@@ -456,9 +531,10 @@ void enqueue_pass(pou_ctx* c) {
   g.st = c->st;
   for (int k = 0; k < 2; ++k) {
     g.W[k] = tp<T>(c->W[k]);
-    g.HW[k] = full ? tp<T>(c->Z[k]) : tp<T>(c->HW[k]);
-    g.sigma[k] = full ? c->zero_sigma : c->sigma[k];
+    g.HW[k] = tp<T>(dirb[k]);
+    g.sigma[k] = mat ? c->zero_sigma : c->sigma[k];
   }
+  g.tfac = c->tfac;
   g.trial = 1;
   g.gate = 3;  // skipped on the intermediate steps of Algorithm M (n_org > 1)
   g.ng = c->ng;
@@ -484,8 +560,9 @@ void enqueue_pass(pou_ctx* c) {
   // the FP64 coefficients (the FP32 one as a double-float, hi + lo), so the
   // diagonal is the FP64 norm of (1 + tau sigma) w - tau hw from the
   // H-apply sums.
-  r.trial = full ? 2 : 1;
+  r.trial = mat ? 2 : 1;
   r.dpart = c->dir_dpart;
+  r.tfac = c->tfac;
   for (int k = 0; k < 2; ++k) {
     r.sigma[k] = c->sigma[k];
     r.part[k] = c->part[k];
@@ -499,13 +576,14 @@ void enqueue_pass(pou_ctx* c) {
   ra.st = c->st;
   for (int k = 0; k < 2; ++k) {
     ra.W[k] = tp<T>(c->W[k]);
-    ra.HW[k] = full ? tp<T>(c->Z[k]) : tp<T>(c->HW[k]);
-    ra.sigma[k] = full ? c->zero_sigma : c->sigma[k];
+    ra.HW[k] = tp<T>(dirb[k]);
+    ra.sigma[k] = mat ? c->zero_sigma : c->sigma[k];
     ra.Wout[k] = tp<T>(c->W[k]);
     ra.rho[k] = c->rho[k];
   }
   ra.Rinv = c->Rinv;
   ra.trial = 1;
+  ra.tfac = c->tfac;
   ra.ng = c->ng;
   ra.N = c->N;
   launch_rotate<T>(ra, s);
@@ -573,6 +651,7 @@ void enqueue_pass(pou_ctx* c) {
   k.tau_max = c->cfg.tau_max;
   k.bb_variant = c->cfg.bb_variant;
   k.max_backtrack = c->cfg.max_backtrack;
+  k.tfac = c->cfg.tau_mode == 1 ? c->tfac : nullptr;
   k.n_diag = c->cfg.n_diag;
   k.n_org = c->cfg.n_org;
   for (int q = 0; q < 3; ++q) k.kc[q] = -0.5 * stencil_scale(c, q);
@@ -672,6 +751,7 @@ pou_status init_from_staged(pou_ctx* c) {
   k.init = 1;
   k.dV = c->dV;
   k.tau0 = c->tau0;
+  k.tfac = c->cfg.tau_mode == 1 ? c->tfac : nullptr;
   for (int q = 0; q < 3; ++q) k.kc[q] = -0.5 * stencil_scale(c, q);
   launch_control(k, s);
   pou_status e = check_launch(c, "initialisation kernels");
@@ -919,6 +999,8 @@ void pou_config_default(pou_config* cfg) {
   cfg->n_diag = 0;
   cfg->stream = nullptr;
   cfg->direction = 0;
+  cfg->tau_mode = 0;
+  cfg->solver = 0;
 }
 
 static pou_status create_buffers(pou_ctx* c);
@@ -942,6 +1024,13 @@ pou_status pou_create(const pou_config* cfg, pou_ctx** out) {
   // OptM-QR direction: Algorithm E only (no n_org, no subspace diagonalisation)
   if (cfg->direction != 0 && cfg->direction != 1) return POU_EINVAL;
   if (cfg->direction == 1 && (cfg->n_org != 1 || cfg->n_diag != 0)) return POU_EINVAL;
+  // per-orbital steps and the conjugate-gradient solver: Opt-Par directions, Algorithm E
+  if (cfg->tau_mode != 0 && cfg->tau_mode != 1) return POU_EINVAL;
+  if (cfg->solver != 0 && cfg->solver != 1) return POU_EINVAL;
+  if ((cfg->tau_mode == 1 || cfg->solver == 1) &&
+      (cfg->direction != 0 || cfg->n_org != 1 || cfg->n_diag != 0))
+    return POU_EINVAL;
+  if (cfg->tau_mode == 1 && cfg->solver == 1) return POU_EINVAL;  // CG takes its own per-orbital steps
   // N > 128: FP32 form only, without the subspace diagonalisation
   if (cfg->N > POU_MAX_N_FP64 && (cfg->precision != POU_FP32 || cfg->n_diag > 0)) return POU_EINVAL;
   const long long ng = (long long)cfg->n[0] * cfg->n[1] * cfg->n[2];
@@ -1035,9 +1124,20 @@ static pou_status create_buffers(pou_ctx* c) {
     const int dg = direction_grid(c->ng);
     DALLOC(c->dir_opart, (size_t)dg * c->N * 3 * sizeof(double));
     DALLOC(c->dir_bpart, (size_t)dg * 3 * sizeof(double));
+  }
+  if (cfg->direction == 1 || cfg->solver == 1) {
     DALLOC(c->dir_dpart, (size_t)c->N * 3 * sizeof(double));
     DALLOC(c->zero_sigma, (size_t)c->N * sizeof(double));
     CK(cudaMemsetAsync(c->zero_sigma, 0, (size_t)c->N * sizeof(double), c->stream));
+  }
+  if (cfg->tau_mode == 1 || cfg->solver == 1) DALLOC(c->tfac, (size_t)c->N * sizeof(double));
+  if (cfg->solver == 1) {
+    for (int k = 0; k < 2; ++k) {
+      DALLOC(c->D[k], blk);
+      DALLOC(c->Zs[k], blk);
+    }
+    DALLOC(c->cg_opart, (size_t)c->N * cg_chunks(c->ng) * CG_NS * sizeof(double));
+    DALLOC(c->cg_coef, (size_t)c->N * 2 * sizeof(double));
   }
   DALLOC(c->st, sizeof(State));
   CK(cudaMemsetAsync(c->st, 0, sizeof(State), c->stream));
@@ -1058,7 +1158,8 @@ void pou_destroy(pou_ctx* c) {
                   c->sigma[0], c->sigma[1], c->part[0], c->part[1], c->vext, c->work, c->tilepart,
                   c->epart, c->S, c->Rinv, c->split, c->evec, c->dv, c->st, c->hist_E, c->hist_tau, c->info,
                   c->dR, c->dZ, c->tabs.gx, c->fpart, c->ublock, c->gblock, c->rho_e, c->V64_e, c->rimg,
-                  c->Z[0], c->Z[1], c->dir_opart, c->dir_bpart, c->dir_dpart, c->zero_sigma};
+                  c->Z[0], c->Z[1], c->dir_opart, c->dir_bpart, c->dir_dpart, c->zero_sigma,
+                  c->tfac, c->D[0], c->D[1], c->Zs[0], c->Zs[1], c->cg_opart, c->cg_coef};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->dt == 1) {
@@ -1430,7 +1531,8 @@ pou_status pou_get_state(pou_ctx* c, void* blob, size_t* size) {
   // Barzilai-Borwein step differences against them)
   const size_t need = sizeof(BlobHeader) + sizeof(State) + 2 * HIST_MAX * sizeof(double) +
                       (size_t)c->N * (NP + 1) * sizeof(double) + 2 * blk + 2 * c->ng * sizeof(double) +
-                      (c->cfg.direction == 1 ? 2 * blk : 0);
+                      (c->cfg.direction == 1 ? 2 * blk : 0) + (c->cfg.solver == 1 ? 2 * blk : 0) +
+                      (c->cfg.tau_mode == 1 ? (size_t)c->N * sizeof(double) : 0);
   if (!blob) {
     *size = need;
     return POU_OK;
@@ -1475,7 +1577,15 @@ pou_status pou_get_state(pou_ctx* c, void* blob, size_t* size) {
     CK(cudaMemcpy(p, c->W[1 - cur], blk, cudaMemcpyDeviceToHost));
     p += blk;
     CK(cudaMemcpy(p, c->Z[1 - cur], blk, cudaMemcpyDeviceToHost));
+    p += blk;
   }
+  if (c->cfg.solver == 1) {
+    CK(cudaMemcpy(p, c->D[1 - cur], blk, cudaMemcpyDeviceToHost));
+    p += blk;
+    CK(cudaMemcpy(p, c->Zs[1 - cur], blk, cudaMemcpyDeviceToHost));
+    p += blk;
+  }
+  if (c->cfg.tau_mode == 1) CK(cudaMemcpy(p, c->tfac, (size_t)c->N * sizeof(double), cudaMemcpyDeviceToHost));
   *size = need;
   return POU_OK;
 }
@@ -1513,13 +1623,25 @@ pou_status pou_set_state(pou_ctx* c, const void* blob, size_t size) {
   p += c->ng * sizeof(double);
   CK(cudaMemcpy(c->V64[cur], p, c->ng * sizeof(double), cudaMemcpyHostToDevice));
   p += c->ng * sizeof(double);
+  {
+    const size_t extra = (c->cfg.direction == 1 ? 2 * blk : 0) + (c->cfg.solver == 1 ? 2 * blk : 0) +
+                         (c->cfg.tau_mode == 1 ? (size_t)c->N * sizeof(double) : 0);
+    if (h.bytes < (long long)((p - static_cast<const char*>(blob)) + extra))
+      return fail(c, POU_EINVAL, "state blob lacks the history of this context's direction or steps");
+  }
   if (c->cfg.direction == 1) {
-    if ((long long)size < h.bytes || h.bytes < (long long)((p - static_cast<const char*>(blob)) + 2 * blk))
-      return fail(c, POU_EINVAL, "state blob lacks the OptM-QR history");
     CK(cudaMemcpy(c->W[1 - cur], p, blk, cudaMemcpyHostToDevice));
     p += blk;
     CK(cudaMemcpy(c->Z[1 - cur], p, blk, cudaMemcpyHostToDevice));
+    p += blk;
   }
+  if (c->cfg.solver == 1) {
+    CK(cudaMemcpy(c->D[1 - cur], p, blk, cudaMemcpyHostToDevice));
+    p += blk;
+    CK(cudaMemcpy(c->Zs[1 - cur], p, blk, cudaMemcpyHostToDevice));
+    p += blk;
+  }
+  if (c->cfg.tau_mode == 1) CK(cudaMemcpy(c->tfac, p, (size_t)c->N * sizeof(double), cudaMemcpyHostToDevice));
   if (c->dt == 1)
     launch_convert_f64_f32(c->V64[cur], static_cast<float*>(c->V[cur]), c->ng, c->stream);
   CK(cudaMemcpy(c->st, &hs, sizeof hs, cudaMemcpyHostToDevice));

@@ -80,7 +80,9 @@ struct ApplyArgs {
   const T* dV;          // history: V - V' of the trial vs the current pair, formed in FP64
   const double* sigma[2];
   int mode;             // 0: trial vs current, 1: trial without history, 2: explicit W[0],V[0]->HW[0],
-                        // 3: refresh of the current pair after a subspace rotation
+                        // 3: refresh of the current pair after a subspace rotation, 4: the block
+                        // W[cur] with V[cur], sums only, on the first pass of a step (conjugate-gradient
+                        // directions: <d, H d>)
   double* tilepart;     // [N][ntile][NPT] or nullptr
   T out_scale;
   int N, nx, ny, nz, nzc;
@@ -107,6 +109,7 @@ struct GramArgs {
   i64 ng;
   int N;
   double* split;        // [nsplit][npair][ST*ST]
+  const double* tfac;   // trial mode: orbital i steps tau_trial * tfac[i] (nullptr: 1 for all)
 };
 template <typename T>
 int gram_supertile();
@@ -134,12 +137,13 @@ struct GramReduceArgs {
   double dV;
   double* S;            // N*N
   // diagonal replacement for the trial Gram (iteration mode): 1 from the
-  // H-apply sums (Opt-Par), 2 from the OptM-QR direction sums (dpart)
+  // H-apply sums (Opt-Par), 2 from the sums of a materialised direction (dpart)
   int trial;
-  const double* dpart;  // [N][3]: <w,w>, <w,z>, <z,z> of the OptM-QR direction
+  const double* dpart;  // [N][3]: <w,w>, <w,z>, <z,z> of a materialised direction z
   const double* sigma[2];
   const double* part[2];
   int gate;             // see gate_open
+  const double* tfac;   // per-orbital step factors (nullptr: 1)
 };
 void launch_gram_reduce(const GramReduceArgs& a, cudaStream_t s);
 
@@ -164,6 +168,7 @@ struct RotArgs {
   int N;
   int general;          // 1: full matrix (no triangular skip)
   float* rimg;          // FP32 tensor-core rotation with N > 128: scratch of rotate_rimg_bytes(N)
+  const double* tfac;   // trial mode: orbital i steps tau_trial * tfac[i] (nullptr: 1 for all)
 };
 int rotate_grid(i64 ng, int elem_bytes);
 // bytes of the split R^-1 image the FP32 tensor-core rotation needs for N > 128
@@ -216,6 +221,41 @@ void configure_direction();
 template <typename T>
 void launch_direction(const DirArgs<T>& a, cudaStream_t s);
 void launch_direction_control(const DirCtrlArgs& a, cudaStream_t s);
+
+// ---------------------------------------------------------------- conjugate-gradient direction
+template <typename T>
+struct CgArgs {
+  State* st;
+  const T* W[2];
+  const T* HW[2];
+  T* D[2];              // directions: D[cur] written, D[1-cur] the previous step's
+  T* Zs[2];             // z = hw - sigma w: Zs[cur] written, Zs[1-cur] the previous step's
+  const double* sigma[2];
+  const double* coef;   // [N][2]: beta_i, gamma_i (form pass)
+  double* opart;        // [N][nch][CG_NS]
+  i64 ng;
+  int N, nch;
+};
+constexpr int CG_NS = 6;
+struct CgCtrlArgs {
+  State* st;
+  const double* opart;  // [N][nch][CG_NS]
+  int nch, N;
+  double* coef;         // [N][2]
+  const double* sigma[2];
+  const double* tilepart;  // <d,d>, <d,H d> of the H-apply on D (mode 4)
+  int ntile;
+  double* tfac;
+  double* dpart;        // [N][3]
+  double dV, tau0, tau_min, tau_max;
+};
+int cg_chunks(i64 ng);
+template <typename T>
+void launch_cg_dots(const CgArgs<T>& a, cudaStream_t s);
+template <typename T>
+void launch_cg_form(const CgArgs<T>& a, cudaStream_t s);
+void launch_cg_beta(const CgCtrlArgs& a, cudaStream_t s);
+void launch_cg_step(const CgCtrlArgs& a, cudaStream_t s);
 
 // ---------------------------------------------------------------- cholesky
 // reorth_thr > 0: first pass, sets st->reorth when max|S - I| > reorth_thr;
@@ -285,6 +325,7 @@ struct CtrlArgs {
   int init;
   double dV, rho1, delta, eta, tau0, tau_min, tau_max;
   int bb_variant, max_backtrack;
+  double* tfac;         // per-orbital Barzilai-Borwein steps: tau_i = tau * tfac[i] (nullptr: one tau)
   int n_diag;           // subspace diagonalisation period (0: off)
   int n_org;            // Algorithm M: orthonormalise every n_org steps (1: every step)
   int refresh;          // 1: re-reduce the sums of the rotated current pair only

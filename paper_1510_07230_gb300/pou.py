@@ -27,6 +27,8 @@ STATUS_NAMES = {0: "POU_OK", 1: "POU_EINVAL", 2: "POU_ENOMEM", 3: "POU_ECUDA", 4
                 5: "POU_ENAN", 6: "POU_ENOCONV"}
 FP64, FP32 = 0, 1
 OPT_PAR, OPTM_QR = 0, 1  # config direction: per-orbital sigma_ii (the paper's method) or full Sigma
+TAU_SHARED, TAU_PER_ORBITAL = 0, 1  # config tau_mode
+STEEPEST_DESCENT, CONJUGATE_GRADIENT = 0, 1  # config solver
 DT_F64, DT_F32 = 0, 1
 MAX_N = 512       # FP32 form
 MAX_N_FP64 = 128  # FP64 form, subspace diagonalisation
@@ -44,7 +46,8 @@ class Config(C.Structure):
                 ("bb_variant", C.c_int), ("rho1", C.c_double), ("delta", C.c_double),
                 ("eta", C.c_double), ("max_backtrack", C.c_int), ("tau0", C.c_double),
                 ("tau_min", C.c_double), ("tau_max", C.c_double), ("n_org", C.c_int),
-                ("n_diag", C.c_int), ("stream", C.c_void_p), ("direction", C.c_int)]
+                ("n_diag", C.c_int), ("stream", C.c_void_p), ("direction", C.c_int),
+                ("tau_mode", C.c_int), ("solver", C.c_int)]
 
 
 class EnergyTerms(C.Structure):

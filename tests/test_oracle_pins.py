@@ -563,3 +563,93 @@ def test_converged_forces_match_fd_of_reconverged_energies():
             Em = converge(Rm, st.W).E
             fd = (Ep - Em) / (2 * h)
             assert abs(fd - dR[I, a]) < 1e-5, (I, a, fd, dR[I, a])
+
+
+def test_per_orbital_bb_steps_on_separate_quadratics():
+    """tau_i of Sec. 3.2 taken orbital by orbital: when y_i = k_i s_i (orbital
+    i on its own quadratic with Hessian k_i I) both quotients give 1/k_i, and
+    the common step of the traces lies between the smallest and largest."""
+    cfg = O.cubic(6, 3.0, N=3)
+    rng = np.random.default_rng(7)
+    S = rng.standard_normal((3,) + cfg.shape)
+    k = np.array([0.5, 2.0, 8.0])
+    Y = k[:, None, None, None] * S
+    for v in (1, 2):
+        c = O.Config(n=cfg.n, L=cfg.L, bb_variant=v)
+        np.testing.assert_allclose(O.bb_step_per_orbital(S, Y, c, 0), 1.0 / k, rtol=1e-14)
+        t = O.bb_step(S, Y, c, 0)
+        assert 1.0 / k.max() <= t <= 1.0 / k.min()
+
+
+def _rayleigh(u, V, cfg):
+    return float(np.sum(u * O.apply_h(u[None], V, cfg)[0]) / np.sum(u * u))
+
+
+def test_newton_step_is_minus_first_over_second_derivative():
+    """The CG step of each orbital is the Newton step of its Rayleigh quotient
+    R(t) = <u, H u> / <u, u>, u = w_i - t d_i (potential frozen): checked
+    against -R'(0) / R''(0) from central differences of R itself."""
+    cfg = O.Config(n=(10, 9, 8), L=(5.0, 4.5, 4.0), order=4, N=3)
+    R, Zc = inputs.atoms(9, 2, 4.0, "const4")
+    vext = O.vext_gaussians(cfg, R, Zc, 0.8)
+    W, _, _ = O.cholesky_qr(inputs.random_orbitals(9, 3, cfg.n), cfg)
+    V = O.total_potential(O.density(W), vext, cfg)
+    HW = O.apply_h(W, V, cfg)
+    Zd, sigma = O.search_direction(W, HW, cfg)
+    rng = np.random.default_rng(3)
+    D = Zd + 0.3 * rng.standard_normal(W.shape) * np.max(np.abs(Zd))
+    w2 = W.reshape(3, -1)
+    D = (D.reshape(3, -1) - (cfg.dV * np.sum(w2 * D.reshape(3, -1), 1))[:, None] * w2).reshape(W.shape)
+    t = O.newton_steps(D, Zd, V, sigma, cfg)
+    h = 1e-4
+    for i in range(3):
+        r = [_rayleigh(W[i] - s * D[i], V, cfg) for s in (-h, 0.0, h)]
+        d1 = (r[2] - r[0]) / (2 * h)
+        d2 = (r[2] - 2 * r[1] + r[0]) / (h * h)
+        assert abs(t[i] - (-d1 / d2)) < 1e-5 * abs(t[i]), (i, t[i], -d1 / d2)
+
+
+def test_cg_direction_structure():
+    """d_i = z_i on the first step; otherwise d_i - z_i is a non-negative
+    multiple of the previous direction with its w_i component removed, beta_i
+    is zero when z_i = z_i', and every orbital keeps <z_i, d_i> >= <z_i, z_i>/2."""
+    cfg = O.cubic(6, 3.0, N=4)
+    rng = np.random.default_rng(11)
+    W, _, _ = O.cholesky_qr(rng.standard_normal((4,) + cfg.shape), cfg)
+    Zc = rng.standard_normal(W.shape)
+    Zp = rng.standard_normal(W.shape)
+    Dp = rng.standard_normal(W.shape)
+    assert np.array_equal(O.cg_direction(W, Zc, None, None, cfg), Zc)
+    D = O.cg_direction(W, Zc, Zp, Dp, cfg).reshape(4, -1)
+    z, w, dp = Zc.reshape(4, -1), W.reshape(4, -1), Dp.reshape(4, -1)
+    dpp = dp - (cfg.dV * np.sum(w * dp, 1))[:, None] * w
+    for i in range(4):
+        diff = D[i] - z[i]
+        beta = float(np.dot(diff, dpp[i]) / np.dot(dpp[i], dpp[i]))
+        assert beta >= 0.0 and np.allclose(diff, beta * dpp[i], atol=1e-12 * np.max(np.abs(z)))
+        assert np.dot(z[i], D[i]) >= 0.5 * np.dot(z[i], z[i]) - 1e-9
+    # identical gradients: the Polak-Ribiere numerator vanishes
+    assert np.allclose(O.cg_direction(W, Zc, Zc, Dp, cfg), Zc)
+
+
+@pytest.mark.parametrize("kw", [{"tau_mode": 1}, {"solver": 1}])
+def test_per_orbital_steps_and_cg_reach_the_minimum(kw):
+    """Both additions to the subproblem solver reach the minimum Algorithm E
+    reaches (steepest descent with one Barzilai-Borwein step, run to
+    convergence), and every accepted step passes Eq. (ene-de) with the
+    decrease of the step actually taken (here: E never above C)."""
+    cfg0 = O.cubic(16, 7.0, order=4, N=3)
+    R, Z = inputs.atoms(14, 2, 7.0, "const4")
+    vext = O.vext_gaussians(cfg0, R, Z, 0.8)
+    U0 = inputs.random_orbitals(14, 3, cfg0.n)
+    ref = O.run(U0, vext, cfg0, 4000, e_tol=1e-16)
+    cfg = O.cubic(16, 7.0, order=4, N=3, **kw)
+    st = O.initial_state(U0, vext, cfg)
+    for _ in range(60):
+        C = st.C
+        O.iterate(st, vext, cfg)
+        rec = st.history[-1]
+        if not rec.forced:
+            assert rec.energy <= C + 1e-12
+    st = O.run(None, vext, cfg, 4000, e_tol=1e-16, st=st)
+    assert abs(st.E - ref.E) < 1e-9, (st.E - ref.E, len(st.history))
