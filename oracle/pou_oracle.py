@@ -81,6 +81,7 @@ class Config:
     n_diag: int = 0  # Algorithm M: subspace diagonalisation every n_diag steps (0 = off)
     tau_mode: int = 0  # 0: one Barzilai-Borwein step for all orbitals, 1: tau_i per orbital
     solver: int = 0  # per-orbital subproblem solver: 0 steepest descent, 1 conjugate gradient
+    xi: Optional[np.ndarray] = None  # nonlocal projectors xi_p on the grid, (P, nz, ny, nx); None: none
 
     @property
     def h(self):
@@ -192,6 +193,40 @@ def wrap_positions(R: np.ndarray, cfg: Config) -> np.ndarray:
     return R - L[None, :] * np.floor(R / L[None, :])
 
 
+def projectors_gaussian(cfg: Config, centres: np.ndarray, widths: np.ndarray, amps: np.ndarray) -> np.ndarray:
+    """Synthetic nonlocal projectors xi_p(r) = a_p sum_n exp(-|r - c_p - nL|^2 / (2 s_p^2))
+    on the grid (the xi_l of the pseudopotential's nonlocal part, Sec. 2.1),
+    summed over the 27 nearest periodic images of c_p folded into [0, L),
+    evaluated as the product of three per-axis image sums (distributivity)."""
+    x, y, z = grid_coords(cfg)
+    Lx, Ly, Lz = (float(v) for v in cfg.L)
+    C = wrap_positions(centres, cfg)
+    P = len(amps)
+    xi = np.zeros((P,) + cfg.shape)
+    for p in range(P):
+        t = 2.0 * widths[p] ** 2
+        gx = sum(np.exp(-(x - C[p, 0] - a * Lx) ** 2 / t) for a in (-1, 0, 1))
+        gy = sum(np.exp(-(y - C[p, 1] - b * Ly) ** 2 / t) for b in (-1, 0, 1))
+        gz = sum(np.exp(-(z - C[p, 2] - c * Lz) ** 2 / t) for c in (-1, 0, 1))
+        xi[p] = amps[p] * gz[:, None, None] * gy[None, :, None] * gx[None, None, :]
+    return xi
+
+
+def projections(W: np.ndarray, cfg: Config) -> np.ndarray:
+    """C_pi = <xi_p, w_i> (P x N)."""
+    N = W.shape[0]
+    P = cfg.xi.shape[0]
+    return cfg.dV * (cfg.xi.reshape(P, -1) @ W.reshape(N, -1).T)
+
+
+def apply_nonlocal(W: np.ndarray, cfg: Config) -> np.ndarray:
+    """V_nloc w_i = sum_p <xi_p, w_i> xi_p (Sec. 2.1)."""
+    N = W.shape[0]
+    P = cfg.xi.shape[0]
+    C = projections(W, cfg)
+    return (C.T @ cfg.xi.reshape(P, -1)).reshape(W.shape)
+
+
 def density(W: np.ndarray) -> np.ndarray:
     """rho = f * sum_i w_i^2 (Sec. 2.1 with double occupancy)."""
     return F_OCC * np.sum(W * W, axis=0)
@@ -238,11 +273,16 @@ class EnergyTerms:
 
 
 def energy_terms(W: np.ndarray, vext: np.ndarray, cfg: Config) -> EnergyTerms:
-    """Discrete Kohn-Sham energy of Eq. (energy); W need not be orthonormal."""
+    """Discrete Kohn-Sham energy of Eq. (energy); W need not be orthonormal.
+    The external term holds the local part dV sum rho Vext and, with
+    projectors, the nonlocal part f sum_i sum_p <xi_p, w_i>^2 (both are parts
+    of V_ext in Sec. 2.1)."""
     dV = cfg.dV
     rho = density(W)
     ekin = F_OCC * dV * float(np.sum(W * (-0.5 * laplacian(W, cfg))))
     eext = dV * float(np.sum(rho * vext))
+    if cfg.xi is not None:
+        eext += F_OCC * float(np.sum(projections(W, cfg) ** 2))
     eh = 0.0
     if cfg.hartree:
         eh = 0.5 * dV * float(np.sum(rho * hartree_potential(rho, cfg)))
@@ -267,8 +307,12 @@ def total_potential(rho: np.ndarray, vext: np.ndarray, cfg: Config) -> np.ndarra
 
 
 def apply_h(W: np.ndarray, V: np.ndarray, cfg: Config) -> np.ndarray:
-    """H(rho) w_i = -1/2 Lap_h w_i + V w_i for every orbital (E_{u_i} = H u_i, Sec. 2.1)."""
-    return -0.5 * laplacian(W, cfg) + V[None] * W
+    """H(rho) w_i = -1/2 Lap_h w_i + V w_i (+ V_nloc w_i with projectors) for
+    every orbital (E_{u_i} = H u_i, Sec. 2.1)."""
+    out = -0.5 * laplacian(W, cfg) + V[None] * W
+    if cfg.xi is not None:
+        out = out + apply_nonlocal(W, cfg)
+    return out
 
 
 def inner_matrix(A: np.ndarray, B: np.ndarray, cfg: Config) -> np.ndarray:

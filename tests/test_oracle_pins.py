@@ -653,3 +653,79 @@ def test_per_orbital_steps_and_cg_reach_the_minimum(kw):
             assert rec.energy <= C + 1e-12
     st = O.run(None, vext, cfg, 4000, e_tol=1e-16, st=st)
     assert abs(st.E - ref.E) < 1e-9, (st.E - ref.E, len(st.history))
+
+
+def test_projectors_product_form_and_integral():
+    """Nonlocal projectors (Sec. 2.1's xi_l): the per-axis image product equals
+    the literal 27-image sum, and a projector integrates to a (2 pi s^2)^(3/2)."""
+    cfg = O.Config(n=(18, 16, 14), L=(7.0, 6.0, 5.5))
+    c = np.array([[0.3, 5.8, 2.0], [3.5, 2.5, 5.4]])
+    s = np.array([0.7, 0.9])
+    a = np.array([1.5, -0.8])
+    xi = O.projectors_gaussian(cfg, c, s, a)
+    x, y, z = O.grid_coords(cfg)
+    for p in range(2):
+        lit = np.zeros(cfg.shape)
+        for i, j, k in itertools.product((-1, 0, 1), repeat=3):
+            d2 = ((z[:, None, None] - c[p, 2] - k * 5.5) ** 2 + (y[None, :, None] - c[p, 1] - j * 6.0) ** 2
+                  + (x[None, None, :] - c[p, 0] - i * 7.0) ** 2)
+            lit += a[p] * np.exp(-d2 / (2 * s[p] ** 2))
+        np.testing.assert_allclose(xi[p], lit, atol=1e-13)
+        assert abs(cfg.dV * xi[p].sum() - a[p] * (2 * math.pi * s[p] ** 2) ** 1.5) < 1e-6
+
+
+def test_nonlocal_rank_one_lifts_the_constant_mode():
+    """Free particles with one projector xi = alpha phi_0, phi_0 the normalised
+    constant mode (eigenvalue 0 of -1/2 Lap_h): H = -1/2 Lap_h + alpha^2 |phi_0><phi_0|
+    lifts that mode to alpha^2 and leaves the plane waves.  With alpha^2 above the
+    second shell, the 6 lowest states are the first shell: E = 2 * 6 * e_1."""
+    n, L = 8, 6.0
+    cfg0 = O.cubic(n, L, order=2, N=6, hartree=0, exchange=0)
+    e = sorted(0.5 * sum(_symbol(2, m[a], n, L / n) for a in range(3))
+               for m in itertools.product(range(n), repeat=3))
+    e1, e2 = e[1], e[7]
+    alpha = math.sqrt(3.0 * e2)
+    xi = (alpha / math.sqrt(L ** 3)) * np.ones((1,) + cfg0.shape)
+    cfg = O.cubic(n, L, order=2, N=6, hartree=0, exchange=0, xi=xi)
+    st = O.run(inputs.random_orbitals(17, 6, cfg.n), np.zeros(cfg.shape), cfg, 1500, e_tol=1e-15)
+    assert abs(st.E - 2 * 6 * e1) < 1e-9
+    # the constant mode itself carries alpha^2 in the energy
+    phi0 = np.ones((1,) + cfg.shape) / math.sqrt(L ** 3)
+    cfg1 = O.cubic(n, L, order=2, N=1, hartree=0, exchange=0, xi=xi)
+    assert abs(O.energy(phi0, np.zeros(cfg.shape), cfg1) - 2 * alpha ** 2) < 1e-12
+
+
+def test_nonlocal_well_vs_eigsh():
+    """Non-interacting well plus two Gaussian projectors: the converged energy
+    is twice the sum of the lowest eigenvalues of the sparse FD Hamiltonian
+    plus the rank-2 term sum_p dV xi_p xi_p^T, from scipy's eigsh."""
+    cfg0 = O.cubic(12, 8.0, order=4, N=3, hartree=0, exchange=0)
+    R = np.array([[3.1, 4.2, 3.7], [5.3, 3.5, 4.9]])
+    vext = O.vext_gaussians(cfg0, R, np.array([4.0, 3.0]), 0.8)
+    xi = O.projectors_gaussian(cfg0, R, np.array([0.7, 0.9]), np.array([1.2, 0.6]))
+    cfg = O.cubic(12, 8.0, order=4, N=3, hartree=0, exchange=0, xi=xi)
+    H0 = _sparse_h(cfg0, vext)
+    X = xi.reshape(2, -1)
+    op = spla.LinearOperator(H0.shape, matvec=lambda v: H0 @ v + cfg.dV * (X.T @ (X @ v)), dtype=float)
+    ev = np.sort(spla.eigsh(op, k=5, which="SA", tol=1e-13)[0])
+    st = O.run(inputs.random_orbitals(13, 3, cfg.n), vext, cfg, 3000, e_tol=1e-16)
+    assert abs(st.E - 2.0 * ev[:3].sum()) < 1e-8
+
+
+def test_nonlocal_gradient_finite_differences():
+    cfg0 = O.Config(n=(6, 5, 6), L=(4.0, 3.5, 4.5), order=4, N=2)
+    R = np.array([[1.0, 1.2, 2.0], [3.0, 2.5, 0.7]])
+    vext = O.vext_gaussians(cfg0, R, np.array([2.0, 4.0]), 0.8)
+    xi = O.projectors_gaussian(cfg0, R, np.array([0.8, 0.6]), np.array([1.0, 0.7]))
+    cfg = O.Config(n=(6, 5, 6), L=(4.0, 3.5, 4.5), order=4, N=2, xi=xi)
+    U = 0.3 * inputs.random_orbitals(7, 2, cfg.n)
+    g = O.energy_gradient_orbitals(U, vext, cfg)
+    rng = np.random.default_rng(5)
+    eps = 1e-5
+    for _ in range(20):
+        ix = tuple(rng.integers(0, s) for s in U.shape)
+        Up, Um = U.copy(), U.copy()
+        Up[ix] += eps
+        Um[ix] -= eps
+        fd = (O.energy(Up, vext, cfg) - O.energy(Um, vext, cfg)) / (2 * eps)
+        assert abs(fd - g[ix]) <= 1e-7 * max(1.0, np.max(np.abs(g)))
