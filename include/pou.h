@@ -164,6 +164,18 @@ pou_status pou_set_vext(pou_ctx* ctx, const double* vext, int on_device);
  * doubles (x, y, z per atom), Z: M host doubles; width > 0. */
 pou_status pou_set_atoms(pou_ctx* ctx, int M, const double* R, const double* Z, double width);
 
+/* Nonlocal part of the pseudopotential (Sec. 2.1): V_nloc u = sum_p <xi_p, u> xi_p
+ * with P synthetic Gaussian projectors xi_p(r) = amps[p] sum_n
+ * exp(-|r - c_p - nL|^2 / (2 widths[p]^2)) (n over the 27 nearest images of
+ * the centre folded into [0, L)).  centres: P*3 host doubles (x, y, z),
+ * widths, amps: P host doubles; P = 0 removes them (P <= 256).  H gains the
+ * term and the energy's external part gains f sum_i sum_p <xi_p, w_i>^2.
+ * The projectors do not move with the atoms of pou_set_atoms, so dE/dR of
+ * pou_backward covers the local wells only.  Like pou_set_vext, the current
+ * orbitals must be set again afterwards.  EINVAL with solver = 1. */
+#define POU_MAX_PROJ 256
+pou_status pou_set_projectors(pou_ctx* ctx, int P, const double* centres, const double* widths, const double* amps);
+
 /* Load N orbitals (the initialisation of Algorithm B) and orthonormalise them by one
  * Cholesky-QR; then build rho, V and E of the orthonormal block and reset
  * the iteration history (C^0 = E, Q^0 = 1, Sec. 3.2).  U: [N][nz][ny][nx]

@@ -65,6 +65,10 @@ __global__ void __launch_bounds__(KNT) k_control(CtrlArgs a) {
     esum[tid] = s;
   }
   __syncthreads();
+  // nonlocal energy f sum_ip C_ip^2 of the trial (refresh: unchanged by a rotation)
+  double enl = 0.0;
+  if (a.nlC[t] && !a.refresh)
+    for (int idx = tid; idx < N * a.P; idx += KNT) enl += a.nlC[t][idx] * a.nlC[t][idx];
   const double dV = a.dV;
   double kin = 0.0, ss = 0.0, sy = 0.0, yy = 0.0, zz = 0.0;
   __syncthreads();  // part[] complete (P_SIGP reads sigma[cur] before sigma[t] is written)
@@ -89,6 +93,7 @@ __global__ void __launch_bounds__(KNT) k_control(CtrlArgs a) {
   ss = block_sum(ss, sh);
   sy = block_sum(sy, sh);
   yy = block_sum(yy, sh);
+  enl = block_sum(enl, sh);
   if (tid != 0) return;
   if (a.refresh) {
     // rho, V and E are unchanged by a rotation within the span
@@ -99,7 +104,7 @@ __global__ void __launch_bounds__(KNT) k_control(CtrlArgs a) {
   }
 
   const double ekin = F_OCC * dV * kin;
-  const double eext = dV * esum[E_EXT];
+  const double eext = dV * esum[E_EXT] + F_OCC * enl;
   const double eh = 0.5 * dV * esum[E_H];
   const double ex = dV * esum[E_X];
   const double E = ekin + eext + eh + ex;

@@ -225,7 +225,8 @@ __global__ void __launch_bounds__(NT) k_apply_h(ApplyArgs<T> a) {
     const T lap = ihx2 * ex + ihy2 * ey + ihz2 * ez;
     const T kin = T(-0.5) * lap;
     const T vv = g.v[ly][lx];
-    const T h = kin + vv * c;
+    T h = kin + vv * c;
+    if (a.nl) h += a.nl[(i64)orb * ng + idx];
     if (hw) hw[idx] = a.out_scale * h;
     const T zp = h - sigp * c;
     kww.add(c * c);
@@ -258,7 +259,8 @@ __global__ void __launch_bounds__(NT) k_apply_h(ApplyArgs<T> a) {
         }
       }
       const T dvv = g.dv[ly][lx];
-      const T hs = T(-0.5) * (ihx2 * fx + ihy2 * fy + ihz2 * fz) + vv * sc + dvv * qp[R];
+      T hs = T(-0.5) * (ihx2 * fx + ihy2 * fy + ihz2 * fz) + vv * sc + dvv * qp[R];
+      if (a.nls) hs += a.nls[(i64)orb * ng + idx];
       const T b = hs - sigp * sc;  // (hw - hw') - sigma' s
       acc[P_SS] += sc * sc;
       acc[P_SB] += sc * b;
@@ -486,6 +488,10 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_apply_h_pair(App
         ha[e] = T(-0.5) * (ihx2 * ex + ihy2 * ey + ihz2 * ez) + vv * c;
       }
       const i64 idx = zpl0 + (i64)(z - z0) * pl + col;
+      if (a.nl) {
+        ha[0] += a.nl[(i64)orb * ng + idx];
+        if (act1) ha[1] += a.nl[(i64)orb * ng + idx + 1];
+      }
       if (hw) {
         V2 o;
         o.x = a.out_scale * ha[0];
@@ -547,7 +553,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_apply_h_pair(App
           const T vv = e ? vv2.y : vv2.x;
           const T dvv = e ? dv2.y : dv2.x;
           const T wpc = e ? pc.y : pc.x;
-          const T hsv = T(-0.5) * (ihx2 * fx + ihy2 * fy + ihz2 * fz) + vv * sc + dvv * wpc;
+          T hsv = T(-0.5) * (ihx2 * fx + ihy2 * fy + ihz2 * fz) + vv * sc + dvv * wpc;
+          if (a.nls && (e == 0 || act1)) hsv += a.nls[(i64)orb * ng + idx + e];
           const T b = (hsv - sigp * sc) * me;
           const T sm = sc * me;
           acc[P_SS] += sm * sc;
@@ -614,12 +621,14 @@ constexpr int PW = 2 * TXP;     // points per tile row
 constexpr int ROW = PW + 4;     // shared row: two halo cells each side
 constexpr int PFP = 2;          // planes in flight
 
-template <int R, bool HIST>
+template <int R, bool HIST, bool NLT>
 struct Stage {
   float w[TYP + 2 * R][ROW];
   float s[HIST ? TYP + 2 * R : 1][ROW];  // w' on arrival, then s = w - w'
   float v[TYP][PW];
   float dv[HIST ? TYP : 1][PW];          // V - V' on arrival, then (V - V') w'
+  float nl[NLT ? TYP : 1][PW];           // nonlocal part of H w (projectors)
+  float nls[NLT && HIST ? TYP : 1][PW];  // ... of H s
 };
 
 // Per-lane FP32 arithmetic on the pair, each lane rounded as one scalar
@@ -686,11 +695,11 @@ __device__ __forceinline__ void second_diffs(float2 c, float2 xm2, float2 xp2, f
   }
 }
 
-template <int R, bool HIST, bool CUBIC>
-__global__ void __launch_bounds__(NTP, CUBIC ? 3 : 2) k_apply_h_pk(ApplyArgs<float> a) {
+template <int R, bool HIST, bool CUBIC, bool NLT>
+__global__ void __launch_bounds__(NTP, (CUBIC && !NLT) ? 3 : 2) k_apply_h_pk(ApplyArgs<float> a) {
   constexpr int S = R + 2 + PFP;  // ring of planes; also the length of the register queues
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Stage<R, HIST>* ring = reinterpret_cast<Stage<R, HIST>*>(smem_raw);
+  Stage<R, HIST, NLT>* ring = reinterpret_cast<Stage<R, HIST, NLT>*>(smem_raw);
   __shared__ double red[NTP / 32][NPT];
 
   if (a.st && a.st->done) return;
@@ -707,6 +716,8 @@ __global__ void __launch_bounds__(NTP, CUBIC ? 3 : 2) k_apply_h_pk(ApplyArgs<flo
   const float* V = a.V[t];
   const float* wp = HIST ? a.W[cur] + (i64)orb * ng : nullptr;
   const float* dVp = HIST ? a.dV : nullptr;
+  const float* nlp = NLT ? a.nl + (i64)orb * ng : nullptr;
+  const float* nlsp = (NLT && HIST) ? a.nls + (i64)orb * ng : nullptr;
   const float sigp = (HIST || a.mode == 3) ? (float)a.sigma[cur][orb] : 0.f;
 
   const int ntx = (nx + PW - 1) / PW;
@@ -743,7 +754,7 @@ __global__ void __launch_bounds__(NTP, CUBIC ? 3 : 2) k_apply_h_pk(ApplyArgs<flo
   int zw = wrapi(a_first, nz);
   auto issue_next = [&](int k) {
     if (zi < a_last) {
-      Stage<R, HIST>& g = ring[k];
+      Stage<R, HIST, NLT>& g = ring[k];
       const i64 zo = (i64)zw * pl;
       cp_async<8>(&g.w[cy][cx], w + zo + col);
       if (hrow >= 0) cp_async<8>(&g.w[hrow][hcs], w + zo + hcol);
@@ -754,6 +765,10 @@ __global__ void __launch_bounds__(NTP, CUBIC ? 3 : 2) k_apply_h_pk(ApplyArgs<flo
       if (zi >= z0 && zi < z1) {
         cp_async<8>(&g.v[ly][2 * lx], V + zo + col);
         if constexpr (HIST) cp_async<8>(&g.dv[ly][2 * lx], dVp + zo + col);
+        if constexpr (NLT) {
+          cp_async<8>(&g.nl[ly][2 * lx], nlp + zo + col);
+          if constexpr (HIST) cp_async<8>(&g.nls[ly][2 * lx], nlsp + zo + col);
+        }
       }
     }
     cp_commit();
@@ -785,7 +800,7 @@ __global__ void __launch_bounds__(NTP, CUBIC ? 3 : 2) k_apply_h_pk(ApplyArgs<flo
       {
         // plane pa has landed for this thread's own copies: queue its centre
         // values and convert the cells this thread copied
-        Stage<R, HIST>& g = ring[k];
+        Stage<R, HIST, NLT>& g = ring[k];
         const float2 wc = lds2(&g.w[cy][cx]);
         qw[k] = wc;
         if constexpr (HIST) {
@@ -802,7 +817,7 @@ __global__ void __launch_bounds__(NTP, CUBIC ? 3 : 2) k_apply_h_pk(ApplyArgs<flo
       const int z = pa - R;
       if (z < z0 || !act) continue;
       const int iz = (k + S - R) % S;  // queue slot and ring stage of plane z
-      const Stage<R, HIST>& g = ring[iz];
+      const Stage<R, HIST, NLT>& g = ring[iz];
       const float2 c = qw[iz];
       float2 ex, ey, ez;
       second_diffs<R>(c, lds2(&g.w[cy][cx - 2]), lds2(&g.w[cy][cx + 2]), lds2(&g.w[cy - 1][cx]),
@@ -821,6 +836,7 @@ __global__ void __launch_bounds__(NTP, CUBIC ? 3 : 2) k_apply_h_pk(ApplyArgs<flo
         kky.add_prod(c, ey);
         kkz.add_prod(c, ez);
       }
+      if constexpr (NLT) h = add2(h, lds2(&g.nl[ly][2 * lx]));
       if (hw) {
         const i64 idx = zpl0 + (i64)(z - z0) * pl + col;
         *reinterpret_cast<float2*>(hw + idx) = scale_out ? mul2(oscale, h) : h;
@@ -843,6 +859,7 @@ __global__ void __launch_bounds__(NTP, CUBIC ? 3 : 2) k_apply_h_pk(ApplyArgs<flo
         else
           hs = fma2(vv, sc, fma2(cxk, fx, fma2(cyk, fy, mul2(czk, fz))));
         hs = add2(hs, lds2(&g.dv[ly][2 * lx]));  // + (V - V') w'
+        if constexpr (NLT) hs = add2(hs, lds2(&g.nls[ly][2 * lx]));
         const float2 b = fma2(nsig, sc, hs);      // (hw - hw') - sigma' s
         ass = fma2(sc, sc, ass);
         asb = fma2(sc, b, asb);
@@ -888,9 +905,9 @@ __global__ void __launch_bounds__(NTP, CUBIC ? 3 : 2) k_apply_h_pk(ApplyArgs<flo
   }
 }
 
-template <int R, bool HIST>
+template <int R, bool HIST, bool NLT>
 size_t smem_bytes() {
-  return sizeof(Stage<R, HIST>) * (size_t)(R + 2 + PFP);
+  return sizeof(Stage<R, HIST, NLT>) * (size_t)(R + 2 + PFP);
 }
 
 }  // namespace pk
@@ -908,22 +925,26 @@ size_t apply_smem() {
 }  // namespace
 
 void configure_apply_h() {
-  cudaFuncSetAttribute(pk::k_apply_h_pk<1, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)pk::smem_bytes<1, false>());
-  cudaFuncSetAttribute(pk::k_apply_h_pk<1, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)pk::smem_bytes<1, false>());
-  cudaFuncSetAttribute(pk::k_apply_h_pk<1, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)pk::smem_bytes<1, true>());
-  cudaFuncSetAttribute(pk::k_apply_h_pk<1, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)pk::smem_bytes<1, true>());
-  cudaFuncSetAttribute(pk::k_apply_h_pk<2, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)pk::smem_bytes<2, false>());
-  cudaFuncSetAttribute(pk::k_apply_h_pk<2, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)pk::smem_bytes<2, false>());
-  cudaFuncSetAttribute(pk::k_apply_h_pk<2, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)pk::smem_bytes<2, true>());
-  cudaFuncSetAttribute(pk::k_apply_h_pk<2, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)pk::smem_bytes<2, true>());
+#define POU_PK_CFG(R_, H_, C_, N_)                                                                     \
+  cudaFuncSetAttribute(pk::k_apply_h_pk<R_, H_, C_, N_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                       (int)pk::smem_bytes<R_, H_, N_>())
+  POU_PK_CFG(1, false, false, false);
+  POU_PK_CFG(1, false, true, false);
+  POU_PK_CFG(1, true, false, false);
+  POU_PK_CFG(1, true, true, false);
+  POU_PK_CFG(2, false, false, false);
+  POU_PK_CFG(2, false, true, false);
+  POU_PK_CFG(2, true, false, false);
+  POU_PK_CFG(2, true, true, false);
+  POU_PK_CFG(1, false, false, true);
+  POU_PK_CFG(1, false, true, true);
+  POU_PK_CFG(1, true, false, true);
+  POU_PK_CFG(1, true, true, true);
+  POU_PK_CFG(2, false, false, true);
+  POU_PK_CFG(2, false, true, true);
+  POU_PK_CFG(2, true, false, true);
+  POU_PK_CFG(2, true, true, true);
+#undef POU_PK_CFG
   cudaFuncSetAttribute(k_apply_h_pair<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)apply_pair_smem<float, 1>());
   cudaFuncSetAttribute(k_apply_h_pair<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -978,20 +999,30 @@ void launch_apply_h(const ApplyArgs<T>& a0, int order, cudaStream_t s, int* ntil
     if (ts.kind == TILE_PACKED) {
       const bool hist = a.mode == 0;
       const bool cubic = a.cubic != 0;
-#define POU_PK(R_, H_, C_) pk::k_apply_h_pk<R_, H_, C_><<<grid, block, pk::smem_bytes<R_, H_>(), s>>>(a)
+#define POU_PK(R_, H_, C_, N_) \
+  pk::k_apply_h_pk<R_, H_, C_, N_><<<grid, block, pk::smem_bytes<R_, H_, N_>(), s>>>(a)
+#define POU_PK_N(R_, H_, C_)           \
+  do {                                 \
+    if (nlt)                           \
+      POU_PK(R_, H_, C_, true);        \
+    else                               \
+      POU_PK(R_, H_, C_, false);       \
+  } while (0)
+      const bool nlt = a.nl != nullptr;
       if (order == 2) {
         if (hist) {
-          if (cubic) POU_PK(1, true, true); else POU_PK(1, true, false);
+          if (cubic) POU_PK_N(1, true, true); else POU_PK_N(1, true, false);
         } else {
-          if (cubic) POU_PK(1, false, true); else POU_PK(1, false, false);
+          if (cubic) POU_PK_N(1, false, true); else POU_PK_N(1, false, false);
         }
       } else {
         if (hist) {
-          if (cubic) POU_PK(2, true, true); else POU_PK(2, true, false);
+          if (cubic) POU_PK_N(2, true, true); else POU_PK_N(2, true, false);
         } else {
-          if (cubic) POU_PK(2, false, true); else POU_PK(2, false, false);
+          if (cubic) POU_PK_N(2, false, true); else POU_PK_N(2, false, false);
         }
       }
+#undef POU_PK_N
 #undef POU_PK
       prof_end(s);
       if (ntile_out) *ntile_out = ntile;

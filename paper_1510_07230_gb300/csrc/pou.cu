@@ -135,6 +135,16 @@ struct pou_ctx {
   void* Zs[2];
   double* cg_opart;
   double* cg_coef;
+  // nonlocal projectors (pou_set_projectors): per-axis tables and windows,
+  // projections of each pair and of an explicit block, the nonlocal parts of
+  // H w and of H s
+  int P;
+  void* nl_mem;
+  NlTables nlt;
+  double* nlC[2];
+  double* nlCe;
+  void* nl;
+  void* nls;
   State* st;
   double* hist_E;
   double* hist_tau;
@@ -252,6 +262,32 @@ double stencil_scale(const pou_ctx* c, int a) {
   return c->cfg.stencil_order == 2 ? 1.0 / h2 : 1.0 / (12.0 * h2);
 }
 
+// Projections of the block the next H-apply reads and its nonlocal part
+// (sel 1: the trial slot, with the step's part against the current pair when
+// step is set; sel 2: the current slot; sel 0: an explicit block).  No-op
+// without projectors.
+template <typename T>
+void enqueue_nonlocal(pou_ctx* c, int sel, const T* explicit_block, int gate, ApplyArgs<T>* aa, bool step) {
+  if (c->P == 0) return;
+  NlArgs<T> n{};
+  n.st = sel == 0 ? nullptr : c->st;
+  n.tab = c->nlt;
+  for (int k = 0; k < 2; ++k) {
+    n.X[k] = sel == 0 ? explicit_block : tp<T>(c->W[k]);
+    n.C[k] = sel == 0 ? c->nlCe : c->nlC[k];
+  }
+  n.sel = sel;
+  n.nl = tp<T>(c->nl);
+  n.nls = (sel == 1 && step) ? tp<T>(c->nls) : nullptr;
+  n.gate = gate;
+  n.N = c->N;
+  n.dV = c->dV;
+  launch_nl_project<T>(n, c->stream);
+  launch_nl_apply<T>(n, c->stream);
+  aa->nl = tp<T>(c->nl);
+  aa->nls = n.nls;
+}
+
 // 1 when the three per-axis stencil scales are equal, so that the H-apply may
 // keep one kinetic sum for all axes (the FP64 coefficients are then equal).
 int cubic_scales(const pou_ctx* c) {
@@ -360,6 +396,7 @@ void enqueue_diag(pou_ctx* c) {
     aa.sigma[k] = c->sigma[k];
   }
   aa.mode = 3;
+  enqueue_nonlocal<T>(c, 2, nullptr, 2, &aa, false);
   aa.tilepart = c->tilepart;
   aa.out_scale = T(1);
   aa.N = c->N;
@@ -387,6 +424,8 @@ void enqueue_diag(pou_ctx* c) {
   k.refresh = 1;
   k.dV = c->dV;
   for (int q = 0; q < 3; ++q) k.kc[q] = -0.5 * stencil_scale(c, q);
+  for (int q = 0; q < 2; ++q) k.nlC[q] = c->P ? c->nlC[q] : nullptr;
+  k.P = c->P;
   launch_control(k, s);
 }
 
@@ -614,6 +653,7 @@ void enqueue_pass(pou_ctx* c) {
   }
   aa.mode = 0;
   aa.dV = tp<T>(c->dv);
+  enqueue_nonlocal<T>(c, 1, nullptr, 0, &aa, true);
   aa.tilepart = c->tilepart;
   aa.out_scale = T(1);
   aa.N = c->N;
@@ -655,6 +695,8 @@ void enqueue_pass(pou_ctx* c) {
   k.n_diag = c->cfg.n_diag;
   k.n_org = c->cfg.n_org;
   for (int q = 0; q < 3; ++q) k.kc[q] = -0.5 * stencil_scale(c, q);
+  for (int q = 0; q < 2; ++q) k.nlC[q] = c->P ? c->nlC[q] : nullptr;
+  k.P = c->P;
   launch_control(k, s);
 }
 
@@ -722,6 +764,7 @@ pou_status init_from_staged(pou_ctx* c) {
     aa.sigma[k] = c->sigma[k];
   }
   aa.mode = 1;
+  enqueue_nonlocal<T>(c, 1, nullptr, 0, &aa, false);
   aa.tilepart = c->tilepart;
   aa.out_scale = T(1);
   aa.N = c->N;
@@ -753,6 +796,8 @@ pou_status init_from_staged(pou_ctx* c) {
   k.tau0 = c->tau0;
   k.tfac = c->cfg.tau_mode == 1 ? c->tfac : nullptr;
   for (int q = 0; q < 3; ++q) k.kc[q] = -0.5 * stencil_scale(c, q);
+  for (int q = 0; q < 2; ++q) k.nlC[q] = c->P ? c->nlC[q] : nullptr;
+  k.P = c->P;
   launch_control(k, s);
   pou_status e = check_launch(c, "initialisation kernels");
   if (e != POU_OK) return e;
@@ -866,6 +911,7 @@ pou_status eval_block(pou_ctx* c, const T* U, T* HUout, T scale, pou_energy_term
   aa.HW[0] = HUout;
   aa.V[0] = tp<T>(c->V_e);
   aa.mode = 2;
+  enqueue_nonlocal<T>(c, 0, U, 0, &aa, false);
   aa.tilepart = c->tilepart;
   aa.out_scale = scale;
   aa.N = c->N;
@@ -895,8 +941,14 @@ pou_status eval_block(pou_ctx* c, const T* U, T* HUout, T scale, pou_energy_term
     double se[NE] = {0, 0, 0};
     for (int b = 0; b < neblk; ++b)
       for (int q = 0; q < NE; ++q) se[q] += ep[(size_t)b * NE + q];
+    double enl = 0.0;
+    if (c->P) {
+      std::vector<double> Ce((size_t)c->N * c->P);
+      CK(cudaMemcpy(Ce.data(), c->nlCe, Ce.size() * sizeof(double), cudaMemcpyDeviceToHost));
+      for (double v : Ce) enl += v * v;
+    }
     terms->kinetic = F_OCC * c->dV * kin;
-    terms->external = c->dV * se[E_EXT];
+    terms->external = c->dV * se[E_EXT] + F_OCC * enl;
     terms->hartree = 0.5 * c->dV * se[E_H];
     terms->exchange = c->dV * se[E_X];
     terms->total = terms->kinetic + terms->external + terms->hartree + terms->exchange;
@@ -1159,7 +1211,8 @@ void pou_destroy(pou_ctx* c) {
                   c->epart, c->S, c->Rinv, c->split, c->evec, c->dv, c->st, c->hist_E, c->hist_tau, c->info,
                   c->dR, c->dZ, c->tabs.gx, c->fpart, c->ublock, c->gblock, c->rho_e, c->V64_e, c->rimg,
                   c->Z[0], c->Z[1], c->dir_opart, c->dir_bpart, c->dir_dpart, c->zero_sigma,
-                  c->tfac, c->D[0], c->D[1], c->Zs[0], c->Zs[1], c->cg_opart, c->cg_coef};
+                  c->tfac, c->D[0], c->D[1], c->Zs[0], c->Zs[1], c->cg_opart, c->cg_coef,
+                  c->nl_mem, c->nlC[0], c->nlC[1], c->nlCe, c->nl, c->nls};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->dt == 1) {
@@ -1228,6 +1281,111 @@ pou_status pou_set_atoms(pou_ctx* c, int M, const double* R, const double* Z, do
   if (e != POU_OK) return e;
   CK(cudaStreamSynchronize(c->stream));
   c->have_orbitals = false;
+  return POU_OK;
+}
+
+static_assert(POU_MAX_PROJ == kMaxProj, "projector limit of the header and the kernels");
+
+pou_status pou_set_projectors(pou_ctx* c, int P, const double* centres, const double* widths, const double* amps) {
+  if (!c) return POU_EINVAL;
+  if (P < 0 || P > POU_MAX_PROJ) return fail(c, POU_EINVAL, "need 0 <= P <= %d projectors", POU_MAX_PROJ);
+  if (P > 0 && (!centres || !widths || !amps)) return fail(c, POU_EINVAL, "null projector arrays");
+  if (P > 0 && c->cfg.solver == 1)
+    return fail(c, POU_EINVAL, "projectors are not combined with the conjugate-gradient solver");
+  for (int p = 0; p < P; ++p) {
+    if (!(widths[p] > 0.0) || !std::isfinite(widths[p]) || !std::isfinite(amps[p]))
+      return fail(c, POU_EINVAL, "projector %d: width must be > 0 and values finite", p);
+    for (int a = 0; a < 3; ++a)
+      if (!std::isfinite(centres[3 * p + a])) return fail(c, POU_EINVAL, "non-finite projector centre");
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  // the pass changes: the next iterate captures a new graph
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  void* old[] = {c->nl_mem, c->nlC[0], c->nlC[1], c->nlCe, c->nl, c->nls};
+  for (void* q : old)
+    if (q) cudaFree(q);
+  c->nl_mem = c->nl = c->nls = nullptr;
+  c->nlC[0] = c->nlC[1] = c->nlCe = nullptr;
+  c->P = 0;
+  c->nlt = NlTables{};
+  c->have_orbitals = false;  // E and H of the current orbitals change
+  if (P == 0) return POU_OK;
+  const int n[3] = {c->nx, c->ny, c->nz};
+  std::vector<double> tab[3];
+  std::vector<int> win((size_t)P * 6);
+  for (int a = 0; a < 3; ++a) tab[a].assign((size_t)P * n[a], 0.0);
+  for (int p = 0; p < P; ++p) {
+    const double two_s2 = 2.0 * widths[p] * widths[p];
+    for (int a = 0; a < 3; ++a) {
+      const double L = c->cfg.L[a], h = c->h[a];
+      double cp = centres[3 * p + a];
+      cp -= L * std::floor(cp / L);  // folded into [0, L)
+      double* g = tab[a].data() + (size_t)p * n[a];
+      double gmax = 0.0;
+      int kmax = 0;
+      for (int k = 0; k < n[a]; ++k) {
+        double v = 0.0;
+        for (int m = -1; m <= 1; ++m) {
+          const double d = k * h - cp - m * L;
+          v += std::exp(-d * d / two_s2);
+        }
+        g[k] = v;
+        if (v > gmax) {
+          gmax = v;
+          kmax = k;
+        }
+      }
+      // window: the circular run around the peak where the table is >= 1e-14 of its peak
+      const double thr = 1e-14 * gmax;
+      int lo = 0, hi = 0;
+      while (lo < n[a] - 1 && g[(kmax - lo - 1 + n[a]) % n[a]] >= thr) ++lo;
+      while (hi < n[a] - 1 - lo && g[(kmax + hi + 1) % n[a]] >= thr) ++hi;
+      const int len = lo + hi + 1;
+      win[(size_t)p * 6 + 2 * a] = len >= n[a] ? 0 : (kmax - lo + n[a]) % n[a];
+      win[(size_t)p * 6 + 2 * a + 1] = std::min(len, n[a]);
+      if (a == 0)
+        for (int k = 0; k < n[a]; ++k) g[k] *= amps[p];
+    }
+  }
+  const size_t nt = (size_t)P * (n[0] + n[1] + n[2]);
+  const size_t bytes = nt * sizeof(double) + nt * sizeof(float) + win.size() * sizeof(int);
+  DALLOC(c->nl_mem, bytes);
+  double* d = static_cast<double*>(c->nl_mem);
+  float* f = reinterpret_cast<float*>(d + nt);
+  int* w = reinterpret_cast<int*>(f + nt);
+  size_t off = 0;
+  const double* dt[3];
+  const float* ft[3];
+  for (int a = 0; a < 3; ++a) {
+    std::vector<float> tf(tab[a].begin(), tab[a].end());
+    CK(cudaMemcpy(d + off, tab[a].data(), tab[a].size() * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(f + off, tf.data(), tf.size() * sizeof(float), cudaMemcpyHostToDevice));
+    dt[a] = d + off;
+    ft[a] = f + off;
+    off += tab[a].size();
+  }
+  CK(cudaMemcpy(w, win.data(), win.size() * sizeof(int), cudaMemcpyHostToDevice));
+  const size_t blk = (size_t)c->N * c->ng * c->esz;
+  DALLOC(c->nlC[0], (size_t)c->N * P * sizeof(double));
+  DALLOC(c->nlC[1], (size_t)c->N * P * sizeof(double));
+  DALLOC(c->nlCe, (size_t)c->N * P * sizeof(double));
+  DALLOC(c->nl, blk);
+  DALLOC(c->nls, blk);
+  c->nlt.P = P;
+  c->nlt.nx = c->nx;
+  c->nlt.ny = c->ny;
+  c->nlt.nz = c->nz;
+  c->nlt.gx = dt[0];
+  c->nlt.gy = dt[1];
+  c->nlt.gz = dt[2];
+  c->nlt.gxf = ft[0];
+  c->nlt.gyf = ft[1];
+  c->nlt.gzf = ft[2];
+  c->nlt.win = w;
+  c->P = P;
   return POU_OK;
 }
 
@@ -1532,7 +1690,8 @@ pou_status pou_get_state(pou_ctx* c, void* blob, size_t* size) {
   const size_t need = sizeof(BlobHeader) + sizeof(State) + 2 * HIST_MAX * sizeof(double) +
                       (size_t)c->N * (NP + 1) * sizeof(double) + 2 * blk + 2 * c->ng * sizeof(double) +
                       (c->cfg.direction == 1 ? 2 * blk : 0) + (c->cfg.solver == 1 ? 2 * blk : 0) +
-                      (c->cfg.tau_mode == 1 ? (size_t)c->N * sizeof(double) : 0);
+                      (c->cfg.tau_mode == 1 ? (size_t)c->N * sizeof(double) : 0) +
+                      (size_t)c->N * c->P * sizeof(double);
   if (!blob) {
     *size = need;
     return POU_OK;
@@ -1585,7 +1744,11 @@ pou_status pou_get_state(pou_ctx* c, void* blob, size_t* size) {
     CK(cudaMemcpy(p, c->Zs[1 - cur], blk, cudaMemcpyDeviceToHost));
     p += blk;
   }
-  if (c->cfg.tau_mode == 1) CK(cudaMemcpy(p, c->tfac, (size_t)c->N * sizeof(double), cudaMemcpyDeviceToHost));
+  if (c->cfg.tau_mode == 1) {
+    CK(cudaMemcpy(p, c->tfac, (size_t)c->N * sizeof(double), cudaMemcpyDeviceToHost));
+    p += (size_t)c->N * sizeof(double);
+  }
+  if (c->P) CK(cudaMemcpy(p, c->nlC[cur], (size_t)c->N * c->P * sizeof(double), cudaMemcpyDeviceToHost));
   *size = need;
   return POU_OK;
 }
@@ -1625,8 +1788,9 @@ pou_status pou_set_state(pou_ctx* c, const void* blob, size_t size) {
   p += c->ng * sizeof(double);
   {
     const size_t extra = (c->cfg.direction == 1 ? 2 * blk : 0) + (c->cfg.solver == 1 ? 2 * blk : 0) +
-                         (c->cfg.tau_mode == 1 ? (size_t)c->N * sizeof(double) : 0);
-    if (h.bytes < (long long)((p - static_cast<const char*>(blob)) + extra))
+                         (c->cfg.tau_mode == 1 ? (size_t)c->N * sizeof(double) : 0) +
+                         (size_t)c->N * c->P * sizeof(double);
+    if (h.bytes != (long long)((p - static_cast<const char*>(blob)) + extra))
       return fail(c, POU_EINVAL, "state blob lacks the history of this context's direction or steps");
   }
   if (c->cfg.direction == 1) {
@@ -1641,7 +1805,11 @@ pou_status pou_set_state(pou_ctx* c, const void* blob, size_t size) {
     CK(cudaMemcpy(c->Zs[1 - cur], p, blk, cudaMemcpyHostToDevice));
     p += blk;
   }
-  if (c->cfg.tau_mode == 1) CK(cudaMemcpy(c->tfac, p, (size_t)c->N * sizeof(double), cudaMemcpyHostToDevice));
+  if (c->cfg.tau_mode == 1) {
+    CK(cudaMemcpy(c->tfac, p, (size_t)c->N * sizeof(double), cudaMemcpyHostToDevice));
+    p += (size_t)c->N * sizeof(double);
+  }
+  if (c->P) CK(cudaMemcpy(c->nlC[cur], p, (size_t)c->N * c->P * sizeof(double), cudaMemcpyHostToDevice));
   if (c->dt == 1)
     launch_convert_f64_f32(c->V64[cur], static_cast<float*>(c->V[cur]), c->ng, c->stream);
   CK(cudaMemcpy(c->st, &hs, sizeof hs, cudaMemcpyHostToDevice));

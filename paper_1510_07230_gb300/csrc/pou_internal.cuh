@@ -88,6 +88,8 @@ struct ApplyArgs {
   int N, nx, ny, nz, nzc;
   T ihx2, ihy2, ihz2;
   int cubic;            // 1: the three stencil scales are equal (FP64), so one kinetic sum serves
+  const T* nl;          // nonlocal part of H applied to the block (same layout), added to H w; nullptr: none
+  const T* nls;         // ... applied to the step s = w - w' (mode 0), added to H s; nullptr: none
 };
 template <typename T>
 void launch_apply_h(const ApplyArgs<T>& a, int order, cudaStream_t s, int* ntile_out);
@@ -257,6 +259,36 @@ void launch_cg_form(const CgArgs<T>& a, cudaStream_t s);
 void launch_cg_beta(const CgCtrlArgs& a, cudaStream_t s);
 void launch_cg_step(const CgCtrlArgs& a, cudaStream_t s);
 
+// ---------------------------------------------------------------- nonlocal projectors
+constexpr int kMaxProj = 256;  // = POU_MAX_PROJ of pou.h
+struct NlTables {
+  int P, nx, ny, nz;
+  const double* gx;     // [P][nx], amplitude folded in
+  const double* gy;     // [P][ny]
+  const double* gz;     // [P][nz]
+  const float* gxf;     // FP32 copies for the FP32 form
+  const float* gyf;
+  const float* gzf;
+  const int* win;       // [P][6]: start and length of the x, y and z windows (they wrap)
+};
+template <typename T>
+struct NlArgs {
+  const State* st;      // nullptr: explicit block X[0]
+  NlTables tab;
+  const T* X[2];
+  int sel;              // 0: X[0] -> C[0]; 1: trial slot 1-cur; 2: current slot cur
+  double* C[2];         // [N][P] projections C_ip = <xi_p, x_i>
+  T* nl;                // [N][ng]: sum_p xi_p C_ip
+  T* nls;               // trial only: sum_p xi_p (C_ip - C'_ip), C' = C[cur]; nullptr otherwise
+  int gate;             // see gate_open
+  int N;
+  double dV;
+};
+template <typename T>
+void launch_nl_project(const NlArgs<T>& a, cudaStream_t s);
+template <typename T>
+void launch_nl_apply(const NlArgs<T>& a, cudaStream_t s);
+
 // ---------------------------------------------------------------- cholesky
 // reorth_thr > 0: first pass, sets st->reorth when max|S - I| > reorth_thr;
 // reorth_thr < 0: second pass, gated on st->reorth; 0: neither.
@@ -326,6 +358,8 @@ struct CtrlArgs {
   double dV, rho1, delta, eta, tau0, tau_min, tau_max;
   int bb_variant, max_backtrack;
   double* tfac;         // per-orbital Barzilai-Borwein steps: tau_i = tau * tfac[i] (nullptr: one tau)
+  const double* nlC[2]; // projections C_ip of each pair (nullptr: no projectors); the nonlocal energy
+  int P;                // f sum C_ip^2 of the trial joins the external term
   int n_diag;           // subspace diagonalisation period (0: off)
   int n_org;            // Algorithm M: orthonormalise every n_org steps (1: every step)
   int refresh;          // 1: re-reduce the sums of the rotated current pair only

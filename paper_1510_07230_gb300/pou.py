@@ -80,6 +80,7 @@ _SIG = {
     "pou_set_vext": (_I, [_P, _P, _I]),
     "pou_set_atoms": (_I, [_P, _I, _P, _P, _D]),
     "pou_set_orbitals": (_I, [_P, _P, _I, _I]),
+    "pou_set_projectors": (_I, [_P, _I, _P, _P, _P]),
     "pou_iterate": (_I, [_P, _I, _D, _D, C.POINTER(Report)]),
     "pou_energy": (_I, [_P, C.POINTER(EnergyTerms)]),
     "pou_get_orbitals": (_I, [_P, _P, _I, _I]),
@@ -238,6 +239,17 @@ class Solver:
         Z = np.ascontiguousarray(Z, dtype=np.float64)
         self.M = len(Z)
         self._check(_lib.pou_set_atoms(self._ctx, self.M, R.ctypes.data, Z.ctypes.data, float(width)))
+
+    def set_projectors(self, centres, widths, amps):
+        """Nonlocal projectors (pou_set_projectors); an empty set removes them."""
+        c = np.ascontiguousarray(centres, dtype=np.float64).reshape(-1, 3)
+        w = np.ascontiguousarray(widths, dtype=np.float64).ravel()
+        a = np.ascontiguousarray(amps, dtype=np.float64).ravel()
+        if not (len(c) == len(w) == len(a)):
+            raise ValueError("centres, widths and amps need one entry per projector")
+        P = len(w)
+        self._check(_lib.pou_set_projectors(self._ctx, P, c.ctypes.data if P else None,
+                                            w.ctypes.data if P else None, a.ctypes.data if P else None))
 
     def set_orbitals(self, U):
         keep = []
