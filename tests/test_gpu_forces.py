@@ -1,0 +1,85 @@
+"""Converged forces on the differentiation workload (64^3, N = 8, 4 atoms), through the C-ABI.
+
+At the minimum over orthonormal orbitals the derivative of the converged
+energy E*(R) is the explicit dE/dR at fixed orbitals (Sec. 2.1: the orbital
+gradient H u_i lies in the span, so the orbitals' response does not enter).
+FP64: the adjoint's dE/dR of the converged orbitals against the oracle's
+analytic gradient of the same orbitals and against central differences of
+energies re-converged at R +- 1e-4 bohr (to 1e-5 Ha/bohr).  FP32: central
+differences of FP32 energies would be dominated by the energy floor
+(~1e-7 Ha / 2e-4 bohr), so the FP32 converged force is compared with the FP64
+one and with the oracle's gradient of the FP32 orbitals.
+"""
+import numpy as np
+import pytest
+
+from oracle import pou_oracle as O
+from paper_1510_07230_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def P():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1510_07230_gb300 import pou
+    return pou
+
+
+@pytest.fixture(scope="module")
+def converged_fp64(P):
+    w, R, Z, U0 = inputs.workload_inputs("l12_g64_n8")
+    s = P.Solver(w.n, w.L, w.N, order=w.order, precision=P.FP64)
+    s.set_atoms(R, Z, w.width)
+    s.set_orbitals(U0)
+    rep = s.iterate(6000, grad_tol=1e-7)
+    assert rep["converged"] == 2, rep
+    W = s.get_orbitals()
+    _, dR, dZ = s.backward(None, 1.0, None, atoms=True)
+    yield w, R, Z, s, W, dR, dZ
+    s.close()
+
+
+def test_fp64_converged_force_against_oracle_gradient(P, converged_fp64):
+    w, R, Z, s, W, dR, dZ = converged_fp64
+    cfg = O.cubic(w.n, w.L, order=w.order, N=w.N)
+    rR, rZ = O.energy_gradient_atoms(W, cfg, R, Z, w.width)
+    assert np.max(np.abs(dR - rR)) < 1e-8 * max(1.0, np.max(np.abs(rR)))
+    assert np.max(np.abs(dZ - rZ)) < 1e-8 * max(1.0, np.max(np.abs(rZ)))
+    assert np.max(np.abs(dR)) > 1e-2  # the atoms feel real forces
+
+
+def test_fp64_converged_force_against_reconverged_energies(P, converged_fp64):
+    w, R, Z, s, W, dR, _ = converged_fp64
+    h = 1e-4
+    for I, a in ((0, 0), (0, 1), (0, 2), (2, 0), (3, 2)):
+        E = []
+        for sign in (1.0, -1.0):
+            Rs = R.copy()
+            Rs[I, a] += sign * h
+            t = P.Solver(w.n, w.L, w.N, order=w.order, precision=P.FP64)
+            t.set_atoms(Rs, Z, w.width)
+            t.set_orbitals(W)
+            rep = t.iterate(4000, grad_tol=1e-7)
+            assert rep["converged"] == 2
+            E.append(t.energy()["total"])
+            t.close()
+        fd = (E[0] - E[1]) / (2 * h)
+        assert abs(fd - dR[I, a]) < 1e-5, (I, a, fd, dR[I, a])
+
+
+def test_fp32_converged_force(P, converged_fp64):
+    w, R, Z, _, _, dR64, _ = converged_fp64
+    s = P.Solver(w.n, w.L, w.N, order=w.order, precision=P.FP32)
+    s.set_atoms(R, Z, w.width)
+    s.set_orbitals(inputs.workload_inputs("l12_g64_n8")[3])
+    s.iterate(4000)
+    W = s.get_orbitals()
+    _, dR, _ = s.backward(None, 1.0, None, atoms=True)
+    cfg = O.cubic(w.n, w.L, order=w.order, N=w.N)
+    rR, _ = O.energy_gradient_atoms(W, cfg, R, Z, w.width)
+    assert np.max(np.abs(dR - rR)) < 1e-6 * max(1.0, np.max(np.abs(rR)))
+    assert np.max(np.abs(dR - dR64)) < 1e-4, np.max(np.abs(dR - dR64))
+    s.close()
