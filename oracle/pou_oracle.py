@@ -335,6 +335,28 @@ def cholesky_qr(Wt: np.ndarray, cfg: Config):
     return Xn.reshape(Wt.shape), S, R
 
 
+PIVOT_REL = 1e-13  # a Cholesky pivot below this fraction of max S_ii counts as singular
+TAU_SPREAD = 10.0  # per-orbital steps stay within this factor of the common step
+
+
+def try_cholesky_qr(Wt: np.ndarray, cfg: Config):
+    """Cholesky-QR of a trial block, or None when its Gram matrix is not
+    numerically positive definite: a pivot (R_kk^2) at or below PIVOT_REL
+    times the largest diagonal entry of S, or a failed factorisation.  The
+    iteration rejects such a trial like one failing Eq. (ene-de)."""
+    N = Wt.shape[0]
+    X = Wt.reshape(N, -1)
+    S = cfg.dV * (X @ X.T)
+    try:
+        R = cholesky(S, lower=False)
+    except np.linalg.LinAlgError:
+        return None
+    if not np.all(np.isfinite(R)) or np.min(np.diag(R)) ** 2 <= PIVOT_REL * np.max(np.diag(S)):
+        return None
+    Xn = solve_triangular(R, X, trans="T", lower=False)
+    return Xn.reshape(Wt.shape), S, R
+
+
 def gradient_residual(W: np.ndarray, HW: np.ndarray, cfg: Config) -> float:
     """||grad E||_F = sqrt(tr<G^T G>), G = HW - W Sigma, Sigma = <(HW)^T W> (Eq. gra)."""
     N = W.shape[0]
@@ -520,7 +542,9 @@ def iterate(st: State, vext: np.ndarray, cfg: Config, full_sigma: bool = False) 
         tau = float(np.mean(tsteps))
         fac = tsteps / tau
     elif cfg.tau_mode == 1 and st.W_prev is not None:
-        fac = bb_step_per_orbital(W - st.W_prev, Z - st.Z_prev, cfg, st.l) / tau
+        # each orbital's own quotient, kept within TAU_SPREAD of the common step
+        fac = np.clip(bb_step_per_orbital(W - st.W_prev, Z - st.Z_prev, cfg, st.l) / tau,
+                      1.0 / TAU_SPREAD, TAU_SPREAD)
 
     orth_step = (st.l % max(cfg.n_org, 1)) == 0
     if not orth_step:
@@ -540,7 +564,15 @@ def iterate(st: State, vext: np.ndarray, cfg: Config, full_sigma: bool = False) 
     while True:
         t = tau * cfg.delta ** backtracks
         Wt = W - t * fac[:, None, None, None] * D
-        Wn, Sg, _ = cholesky_qr(Wt, cfg)
+        orth = try_cholesky_qr(Wt, cfg)
+        if orth is None:
+            # a trial without a positive definite Gram matrix is rejected like
+            # one failing Eq. (ene-de); past max_backtrack it is a breakdown
+            if backtracks >= cfg.max_backtrack:
+                raise np.linalg.LinAlgError("trial Gram matrix not positive definite")
+            backtracks += 1
+            continue
+        Wn, Sg, _ = orth
         En = energy(Wn, vext, cfg)
         if En <= st.C - cfg.rho1 * t * decrease:
             break

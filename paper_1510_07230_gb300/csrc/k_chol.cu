@@ -28,7 +28,7 @@ constexpr int MAXB = 4;      // panels for N <= 128
 
 __global__ void __launch_bounds__(CNT) k_cholinv(const State* st_ro, State* st, const double* S,
                                                   double* Rinv, int N, int* info, double piv_rel,
-                                                  double reorth_thr, int orth_gated) {
+                                                  double reorth_thr, int orth_gated, int soft_limit) {
   extern __shared__ double A[];  // [N][N+1]: upper = R, strictly lower = X^T
   __shared__ double rdiag[128];  // 1 / R_ii
   __shared__ double T[MAXB - 1][NB][NB + 1];  // sums of one level of the inverse
@@ -165,8 +165,12 @@ __global__ void __launch_bounds__(CNT) k_cholinv(const State* st_ro, State* st, 
       if (info) *info = fail;
       if (st) {
         st->chol_info = fail;
-        st->status = 4;  // POU_ENOTSPD
-        st->done = 1;
+        if (soft_limit >= 0 && st->s < soft_limit) {
+          st->chol_fail = 1;  // the controller rejects the trial and shrinks the step
+        } else {
+          st->status = 4;  // POU_ENOTSPD
+          st->done = 1;
+        }
       }
     }
     return;
@@ -249,6 +253,7 @@ struct BigArgs {
   int* flag;        // 0, or 1 + the failing pivot
   double piv_rel, reorth_thr;
   int orth_gated;   // trial pass: skipped (R^-1 = I) on the intermediate steps of Algorithm M
+  int soft_limit;   // >= 0: a failing pivot rejects the trial while State::s < soft_limit
 };
 
 __device__ __forceinline__ bool big_intermediate(const BigArgs& a) {
@@ -344,8 +349,12 @@ __global__ void __launch_bounds__(32) k_big_diag(BigArgs a, int p) {
       *a.flag = fail;
       if (a.st_rw) {
         a.st_rw->chol_info = fail;
-        a.st_rw->status = 4;  // POU_ENOTSPD
-        a.st_rw->done = 1;
+        if (a.soft_limit >= 0 && a.st_rw->s < a.soft_limit) {
+          a.st_rw->chol_fail = 1;
+        } else {
+          a.st_rw->status = 4;  // POU_ENOTSPD
+          a.st_rw->done = 1;
+        }
       }
     }
     return;
@@ -499,10 +508,11 @@ __global__ void __launch_bounds__(256) k_big_final(BigArgs a, int* info) {
 }
 
 void launch_cholinv_big(const State* st, const double* S, double* Rinv, int N, int* info, State* st_rw,
-                        double piv_rel, double reorth_thr, cudaStream_t s, bool orth_gated) {
+                        double piv_rel, double reorth_thr, cudaStream_t s, bool orth_gated, int soft_limit) {
   // the failing-pivot flag: the caller's info, else the iteration state's chol_info
   if (!info && !st_rw) return;
-  BigArgs a{st, st_rw, S, Rinv, N, info ? info : &st_rw->chol_info, piv_rel, reorth_thr, orth_gated ? 1 : 0};
+  BigArgs a{st,       st_rw,      S, Rinv, N, info ? info : &st_rw->chol_info, piv_rel, reorth_thr,
+            orth_gated ? 1 : 0, soft_limit};
   const int np = (N + BT - 1) / BT;
   k_big_init<<<1, 1024, 0, s>>>(a);
   for (int p = 0; p < np; ++p) {
@@ -527,13 +537,13 @@ void configure_cholinv() {
 }
 
 void launch_cholinv(const State* st, const double* S, double* Rinv, int N, int* info, State* st_rw,
-                    double piv_rel, double reorth_thr, cudaStream_t s, bool orth_gated) {
+                    double piv_rel, double reorth_thr, cudaStream_t s, bool orth_gated, int soft_limit) {
   prof_begin("cholinv", s);
   if (N <= 128) {  // one CTA is faster here than the multi-kernel path (0.34 vs 0.38 ms)
     k_cholinv<<<1, CNT, cholinv_smem_bytes(N), s>>>(st, st_rw, S, Rinv, N, info, piv_rel, reorth_thr,
-                                                     orth_gated ? 1 : 0);
+                                                     orth_gated ? 1 : 0, soft_limit);
   } else {
-    launch_cholinv_big(st, S, Rinv, N, info, st_rw, piv_rel, reorth_thr, s, orth_gated);
+    launch_cholinv_big(st, S, Rinv, N, info, st_rw, piv_rel, reorth_thr, s, orth_gated, soft_limit);
   }
   prof_end(s);
 }

@@ -21,6 +21,7 @@ namespace pou {
 namespace {
 
 constexpr int KNT = 256;
+constexpr double kTauSpread = 10.0;  // per-orbital steps stay within this factor of the common one
 
 __device__ double block_sum(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -116,6 +117,17 @@ __global__ void __launch_bounds__(KNT) k_control(CtrlArgs a) {
   ss *= dV;
   sy = fabs(sy * dV);
   yy *= dV;
+  if (!a.init && st->chol_fail) {
+    // the trial's Gram matrix was not positive definite: rejected like a
+    // trial failing Eq. (ene-de), the step shrinks (the Cholesky kernel turns
+    // it into a breakdown once max_backtrack reductions are spent)
+    st->chol_fail = 0;
+    st->passes += 1;
+    st->s += 1;
+    st->backtracks += 1;
+    st->tau_trial = st->tau_bb * pow(a.delta, (double)st->s);
+    return;
+  }
   if (!isfinite(E)) {
     st->status = 5;  // POU_ENAN
     st->done = 1;
@@ -206,7 +218,9 @@ __global__ void __launch_bounds__(KNT) k_control(CtrlArgs a) {
       double ti = (variant == 1) ? (syi > 0.0 ? ssi / syi : NAN) : (yyi > 0.0 ? syi / yyi : NAN);
       if (!isfinite(ti) || ti <= 0.0) ti = a.tau0;
       ti = fmin(fmax(ti, a.tau_min), a.tau_max);
-      const double fi = ti / tau;
+      // within a factor kTauSpread of the common step: an orbital whose own
+      // <s_i, y_i> is near zero cannot take over the trial
+      const double fi = fmin(fmax(ti / tau, 1.0 / kTauSpread), kTauSpread);
       a.tfac[i] = fi;
       zf += fi * (p[P_ZZ] - 2.0 * ds * p[P_ZW] + ds * ds * p[P_WW]);
     }

@@ -297,7 +297,7 @@ int cubic_scales(const pou_ctx* c) {
 // Second Cholesky-QR pass on the block just written to W[1-cur], gated on
 // st->reorth (FP32 form only).
 template <typename T>
-void enqueue_second_orth(pou_ctx* c) {
+void enqueue_second_orth(pou_ctx* c, int soft_limit) {
   if (c->dt != 1) return;
   cudaStream_t s = c->stream;
   GramArgs<T> g{};
@@ -323,7 +323,7 @@ void enqueue_second_orth(pou_ctx* c) {
   r.S = c->S;
   r.gate = 1;
   launch_gram_reduce(r, s);
-  launch_cholinv(c->st, c->S, c->Rinv, c->N, nullptr, c->st, pivot_tol(c), -1.0, s);
+  launch_cholinv(c->st, c->S, c->Rinv, c->N, nullptr, c->st, pivot_tol(c), -1.0, s, false, soft_limit);
   RotArgs<T> ra{};
   ra.rimg = c->rimg;
   ra.st = c->st;
@@ -608,7 +608,8 @@ void enqueue_pass(pou_ctx* c) {
   }
   launch_gram_reduce(r, s);
   // Cholesky and R^-1 in FP64 (R^-1 = I on the intermediate steps of Algorithm M)
-  launch_cholinv(c->st, c->S, c->Rinv, c->N, nullptr, c->st, pivot_tol(c), reorth_thr(c), s, true);
+  launch_cholinv(c->st, c->S, c->Rinv, c->N, nullptr, c->st, pivot_tol(c), reorth_thr(c), s, true,
+                 c->cfg.max_backtrack);
   // W_new = Wt R^-1 and rho into the other pair
   RotArgs<T> ra{};
   ra.rimg = c->rimg;
@@ -626,7 +627,7 @@ void enqueue_pass(pou_ctx* c) {
   ra.ng = c->ng;
   ra.N = c->N;
   launch_rotate<T>(ra, s);
-  enqueue_second_orth<T>(c);
+  enqueue_second_orth<T>(c, c->cfg.max_backtrack);
   // Hartree potential, V and the energy sums of the trial density
   PotArgs<T> pa{};
   pa.st = c->st;
@@ -741,7 +742,7 @@ pou_status init_from_staged(pou_ctx* c) {
   ra.ng = c->ng;
   ra.N = c->N;
   launch_rotate<T>(ra, s);
-  enqueue_second_orth<T>(c);
+  enqueue_second_orth<T>(c, -1);
   PotArgs<T> pa{};
   pa.st = c->st;
   for (int k = 0; k < 2; ++k) {
@@ -1022,6 +1023,7 @@ void pou::configure_kernels() {
   configure_apply_h();
   configure_gram_tc();
   configure_direction();
+  configure_nonlocal();
   configure_rotate_tc();
   done = true;
 }

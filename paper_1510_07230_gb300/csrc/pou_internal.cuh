@@ -56,6 +56,7 @@ struct State {
   int diag_now;      // 1: subspace diagonalisation due before the next trial (Algorithm M)
   int diag_count;
   int orth_now;      // 1: the next trial is orthonormalised (Algorithm M: every n_org steps)
+  int chol_fail;     // 1: the pending trial's Gram matrix was not positive definite (rejected)
 };
 
 // Gate of the optional kernels of a pass: 0 always run, 1 second Cholesky-QR
@@ -288,12 +289,17 @@ template <typename T>
 void launch_nl_project(const NlArgs<T>& a, cudaStream_t s);
 template <typename T>
 void launch_nl_apply(const NlArgs<T>& a, cudaStream_t s);
+void configure_nonlocal();
 
 // ---------------------------------------------------------------- cholesky
 // reorth_thr > 0: first pass, sets st->reorth when max|S - I| > reorth_thr;
 // reorth_thr < 0: second pass, gated on st->reorth; 0: neither.
+// soft_limit >= 0 (trials of the iteration): a failing pivot rejects the
+// trial (State::chol_fail) while State::s < soft_limit; otherwise, and with
+// soft_limit < 0, it is a breakdown (POU_ENOTSPD).
 void launch_cholinv(const State* st, const double* S, double* Rinv, int N, int* info,
-                    State* st_rw, double piv_rel, double reorth_thr, cudaStream_t s, bool orth_gated = false);
+                    State* st_rw, double piv_rel, double reorth_thr, cudaStream_t s, bool orth_gated = false,
+                    int soft_limit = -1);
 size_t cholinv_smem_bytes(int N);
 
 // ---------------------------------------------------------------- fft / potential

@@ -729,3 +729,19 @@ def test_nonlocal_gradient_finite_differences():
         Um[ix] -= eps
         fd = (O.energy(Up, vext, cfg) - O.energy(Um, vext, cfg)) / (2 * eps)
         assert abs(fd - g[ix]) <= 1e-7 * max(1.0, np.max(np.abs(g)))
+
+
+def test_trial_without_positive_definite_gram_is_refused():
+    """A rank-deficient trial block has no Cholesky-QR: try_cholesky_qr
+    refuses it (the iteration then shrinks the step), and agrees with
+    cholesky_qr on a well-conditioned block."""
+    cfg = O.cubic(6, 3.0, N=3)
+    U = inputs.random_orbitals(4, 3, cfg.n)
+    W, S, R = O.cholesky_qr(U, cfg)
+    W2, S2, R2 = O.try_cholesky_qr(U, cfg)
+    assert np.array_equal(W, W2) and np.array_equal(R, R2)
+    Ud = U.copy()
+    Ud[2] = 0.5 * Ud[0] - 2.0 * Ud[1]
+    assert O.try_cholesky_qr(Ud, cfg) is None
+    Ud[2] += 1e-9 * U[2]  # numerically singular: pivot ~1e-18 of S_max
+    assert O.try_cholesky_qr(Ud, cfg) is None
