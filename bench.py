@@ -40,7 +40,7 @@ def metric_name(w, precision="fp32"):
     """The metric line for a workload: the default one is the benchmark's."""
     if w.name == "l30_g160_n128" and precision == "fp32":
         return METRIC
-    form = "mixed form" if precision == "fp32" else "FP64 form"
+    form = {"fp32": "mixed form", "tf32": "mixed form, single-product TF32 Gram"}.get(precision, "FP64 form")
     return f"outer iterations/s ({w.n}^3, N={w.N}, {7 if w.order == 2 else 13}-point, {form})"
 UNIT = "iterations/s"
 HIST_ENTRIES = 16384  # energies the library keeps per run (pou_get_history)
@@ -56,7 +56,8 @@ def parse():
                          "are in the steady regime of a run")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="l30_g160_n128")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "fp64"],
+                    help="fp32: mixed form with TF32x3 split products; tf32: single-product TF32 Gram; fp64")
     ap.add_argument("--bb-variant", type=int, default=3)
     ap.add_argument("--force-every", type=int, default=10)
     ap.add_argument("--fp64-steps", type=int, default=3)
@@ -313,7 +314,7 @@ def run_ours(args):
     big = w.N * w.n ** 3 * 8 > (4 << 30)
     U0 = inputs.random_orbitals(w.seed, w.N, (w.n, w.n, w.n), dtype=np.float32 if big else np.float64)
     gen_s = time.time() - t0
-    prec = pou.FP32 if args.precision == "fp32" else pou.FP64
+    prec = {"fp32": pou.FP32, "tf32": pou.FP32_TF32, "fp64": pou.FP64}[args.precision]
     stream = torch.cuda.Stream()
     s = make_solver(pou, w, prec, stream.cuda_stream, args.bb_variant)
     s.set_atoms(R, Z, w.width)
@@ -372,7 +373,7 @@ def run_ours(args):
     s.set_profiling(False)
 
     # roofline of the dominant kernel (live CUDA-event times on the library's stream)
-    esz = 4 if prec == pou.FP32 else 8
+    esz = 4 if prec != pou.FP64 else 8
     ng = w.n ** 3
     dom = max(prof.items(), key=lambda kv: kv[1][1])
     name, (nl, tms) = dom
@@ -398,23 +399,26 @@ def run_ours(args):
                       "gbs": round(b / (t_ / eff / 1e3) / 1e9, 1) if (b and eff) else None}
         if k in gated:
             kernels[k]["taken"] = eff
-        if k in ("gram", "gram_reorth", "gram_plain") and prec == pou.FP32 and eff:
+        if k in ("gram", "gram_reorth", "gram_plain") and prec != pou.FP64 and eff:
             # tensor-core rate of the TF32 split products actually issued (per
             # 8 grid points, M=N=128, K=8 MMAs: two on each diagonal 128-block,
             # three on each off-diagonal one) and the Gram's own algorithmic
             # flops (upper triangle)
             nsup = (w.N + 127) // 128
-            mmas = 2 * nsup + 3 * nsup * (nsup - 1) // 2
+            mmas = (nsup + nsup * (nsup - 1) // 2) if prec == pou.FP32_TF32 else (2 * nsup + 3 * nsup * (nsup - 1) // 2)
             kernels[k]["tensor_tflops_issued"] = round(mmas * 2 * 128 * 128 * ng / (t_ / eff / 1e3) / 1e12, 1)
             kernels[k]["gram_tflops"] = round(gram_flops(w.N, ng) / (t_ / eff / 1e3) / 1e12, 2)
     iter_kernels = [k for k in prof if k not in ("density", "forces", "potential_local", "convert", "scale_copy")]
     out = {
         "metric": metric_name(w, args.precision), "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if prec == pou.FP32 else "f64", "data": "synthetic",
+        "dtype": "f32" if prec != pou.FP64 else "f64", "data": "synthetic",
         "config": {"workload": args.workload, "grid": f"{w.n}^3", "L_bohr": w.L, "stencil_points": 7 if w.order == 2 else 13,
-                   "atoms": w.n_atoms, "N": w.N, "precision": "mixed: FP32 bulk, FP64 Cholesky/FFT/energies"
-                   if prec == pou.FP32 else "FP64", "bb_variant": args.bb_variant, "forces_every": fe,
+                   "atoms": w.n_atoms, "N": w.N, "precision": {
+                       pou.FP32: "mixed: FP32 bulk, TF32x3 Gram and rotation, FP64 Cholesky/FFT/energies",
+                       pou.FP32_TF32: "mixed: FP32 bulk, single-product TF32 Gram, TF32x3 rotation, FP64 "
+                                      "Cholesky/FFT/energies",
+                       pou.FP64: "FP64"}[prec], "bb_variant": args.bb_variant, "forces_every": fe,
                    "l2": "inputs larger than L2 (orbital block %.2f GB)" % (w.N * ng * esz / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "nonlocal_projectors": len(Z) if args.projectors else 0,
@@ -428,7 +432,7 @@ def run_ours(args):
     out["_iter_kernels"] = iter_kernels
 
     # FP64 form beside it (same workload, same U0)
-    if prec == pou.FP32 and args.fp64_steps > 0 and w.N <= pou.MAX_N_FP64:
+    if prec != pou.FP64 and args.fp64_steps > 0 and w.N <= pou.MAX_N_FP64:
         s64 = make_solver(pou, w, pou.FP64, stream.cuda_stream, args.bb_variant)
         s64.set_atoms(R, Z, w.width)
         s64.set_orbitals(U0)
@@ -448,7 +452,7 @@ def run_ours(args):
     # end to end through the public API with host buffers
     if not args.no_e2e:
         Kh = max(5, min(K, 20))
-        host = torch.empty(U0.shape, dtype=torch.float32 if prec == pou.FP32 else torch.float64, pin_memory=True)
+        host = torch.empty(U0.shape, dtype=torch.float32 if prec != pou.FP64 else torch.float64, pin_memory=True)
         s.get_orbitals(host)  # the orbitals the timed steps ended with: same regime
         outh = torch.empty_like(host, pin_memory=True)
         torch.cuda.synchronize()

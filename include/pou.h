@@ -64,10 +64,17 @@ typedef enum {
 
 /* Arithmetic of the bulk (orbital blocks, stencil, Gram, rotation). */
 typedef enum {
-  POU_FP64 = 0,  /* plain method: everything in FP64 */
-  POU_FP32 = 1   /* mixed: FP32 orbitals/stencil/potential, FP32 Gram and
-                    rotation with FP64 promotion; FP64 Cholesky, density,
-                    Hartree solve, energies and traces */
+  POU_FP64 = 0,         /* plain method: everything in FP64 */
+  POU_FP32 = 1,         /* mixed: FP32 orbitals/stencil/potential; Gram and rotation on the
+                           tensor cores with TF32 split products (three per product, about
+                           2^-21 relative) and FP64 promotion; FP64 Cholesky, density,
+                           Hartree solve, energies and traces */
+  POU_FP32_TF32X3 = 1,  /* the same form, named by its Gram */
+  POU_FP32_TF32 = 2     /* as POU_FP32 with a single TF32 product (hi hi) in the iteration's
+                           Gram matrices: a third of the tensor-core work of the Gram; its
+                           rounding errors are zero-mean and average over the grid points (the
+                           trial Gram's diagonal stays the FP64 norm of the H-apply sums); the
+                           rotation keeps the split products */
 } pou_precision;
 
 typedef enum { POU_DT_F64 = 0, POU_DT_F32 = 1 } pou_dtype;

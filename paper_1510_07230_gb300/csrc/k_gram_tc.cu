@@ -280,6 +280,10 @@ __global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb)
     }
   } else if (warp == MMA_WARP) {
     // ------------------------------------------------------------ MMA issue
+    // single: one TF32 product hi hi per K step (the plain TF32 form); else
+    // the split products hi hi + hi lo + lo hi (hi hi + 2 hi lo on a
+    // diagonal block)
+    const bool single = a.tf32_single != 0;
     if (lane == 0) {
       int it = 0;
       bool ok = true, issued = false;
@@ -305,8 +309,10 @@ __global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb)
             const uint64_t dih = tc::desc_sw128(ih + 32u * k), dil = tc::desc_sw128(il + 32u * k);
             // D[j][i] (TMEM lane = row of block J)
             tc::mma_tf32(d, djh, dih, IDESC, k == 0 ? 0u : 1u);
-            tc::mma_tf32(d, djh, dil, IDESC, 1u);
-            tc::mma_tf32(d, djl, dih, IDESC, 1u);
+            if (!single) {
+              tc::mma_tf32(d, djh, dil, IDESC, 1u);
+              tc::mma_tf32(d, djl, dih, IDESC, 1u);
+            }
           }
           issued = true;
           tc::mma_commit(empty_bar(s0));
@@ -328,7 +334,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb)
           for (int k = 0; k < 4; ++k) {
             const uint64_t dh = tc::desc_sw128(hi_a + 32u * k), dl = tc::desc_sw128(lo_a + 32u * k);
             tc::mma_tf32(d, dh, dh, IDESC, (first && k == 0) ? 0u : 1u);
-            tc::mma_tf32(d, dh, dl, IDESC, 1u);
+            if (!single) tc::mma_tf32(d, dh, dl, IDESC, 1u);
           }
           issued = true;
           tc::mma_commit(empty_bar(s));

@@ -4,17 +4,18 @@
 // table sums the 27 nearest periodic images), with a window per axis outside
 // which a table is below 1e-14 of its largest value.
 //
-// k_nl_project: C_ip = dV sum_r xi_p(r) x_i(r) over the window box of
-//   projector p, one CTA per (projector, orbital): 32 threads along each
-//   window row, row sums weighted by gy, plane sums weighted by gz and
-//   promoted to FP64 once per plane.
+// k_nl_project + k_nl_reduce: C_ip = dV sum_r xi_p(r) x_i(r).  One CTA per
+//   (orbital, z plane, 32 rows) stages the rows once and forms, for every
+//   projector whose windows meet them, the row dot products over its x
+//   window (working type), weighted by gy and summed in FP64; a second kernel
+//   weights the planes by gz and sums them in a fixed order.
 // k_nl_apply: NL_i(r) = sum_p xi_p(r) C_ip and, for a trial block, the
 //   nonlocal part of H applied to the step, NLS_i(r) = sum_p xi_p(r)
 //   (C_ip - C'_ip) with the current iterate's C' (its two terms are then
 //   formed from the step, like the local part).  One CTA per (orbital, z
-//   plane, 32 rows): the projectors whose z and y windows meet the tile are
-//   listed in a fixed order (ballot and prefix counts), their row
-//   coefficients gy gz C formed once, and every point sums over the list.
+//   plane, 32 x 32 tile): the projectors whose windows meet the tile are
+//   listed in a fixed order (ballot and prefix counts), their column tables
+//   and row coefficients gy gz C staged, and every thread forms 4 columns.
 // The H-apply adds NL to H w and NLS to H s; the controller adds the
 // nonlocal energy f sum C_ip^2 to the external term.
 #include "pou_internal.cuh"
@@ -24,7 +25,9 @@ namespace pou {
 namespace {
 
 constexpr int PNT = 256;
-constexpr int AROWS = 32;
+constexpr int PROWS = 32;  // rows of a projection block
+constexpr int ATX = 32;    // apply tile: columns (4 per thread)
+constexpr int ATY = PNT / (ATX / 4);  // apply tile: rows (32)
 
 template <typename T>
 __device__ __forceinline__ const T* tab_x(const NlTables& t, int p);
@@ -52,77 +55,23 @@ __device__ __forceinline__ int nl_slot(const NlArgs<T>& a) {
   return a.sel == 1 ? 1 - cur : cur;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(PNT) k_nl_project(NlArgs<T> a) {
-  if (a.st && (a.st->done || !gate_open(a.st, a.gate))) return;
-  __shared__ double red[PNT / 32];
-  const NlTables& t = a.tab;
-  const int p = blockIdx.x, i = blockIdx.y;
-  const int slot = nl_slot(a);
-  const int nx = t.nx, ny = t.ny, nz = t.nz;
-  const T* x = a.X[slot] + (i64)i * nx * ny * nz;
-  const int* w = t.win + p * 6;
-  const int x0 = w[0], wx = w[1], y0 = w[2], wy = w[3], z0 = w[4], wz = w[5];
-  const T* gxp = tab_x<T>(t, p);
-  // 32 threads along a window row (coalesced), 8 rows at a time
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  double acc = 0.0;
-  for (int kz = 0; kz < wz; ++kz) {
-    int zz = z0 + kz;
-    if (zz >= nz) zz -= nz;
-    const T gzv = tab_z<T>(t, p, zz);
-    T plane = T(0);  // this thread's share of the plane, promoted once per plane
-    for (int ky = ty; ky < wy; ky += PNT / 32) {
-      int yy = y0 + ky;
-      if (yy >= ny) yy -= ny;
-      const T* row = x + ((i64)zz * ny + yy) * nx;
-      T rs = T(0);
-      for (int kx = tx; kx < wx; kx += 32) {
-        int xx = x0 + kx;
-        if (xx >= nx) xx -= nx;
-        rs += gxp[xx] * row[xx];
-      }
-      plane += tab_y<T>(t, p, yy) * rs;
-    }
-    acc += (double)(gzv * plane);
-  }
-  double v = acc;
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int k = 0; k < PNT / 32; ++k) s += red[k];
-    a.C[slot][(i64)i * t.P + p] = a.dV * s;
-  }
+// Window test on one axis: does [a, a + len) meet the window [w0, w0 + wl)
+// (all modulo n)?
+__device__ __forceinline__ bool meets(int a, int len, int w0, int wl, int n) {
+  if (wl >= n) return true;
+  const int d = (a - w0 + n) % n;
+  return d < wl || d + len > n;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(PNT) k_nl_apply(NlArgs<T> a) {
-  if (a.st && (a.st->done || !gate_open(a.st, a.gate))) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const NlTables& t = a.tab;
-  const int nx = t.nx, ny = t.ny, nz = t.nz, P = t.P;
-  T* q = reinterpret_cast<T*>(smem_raw);   // [P][AROWS]: gy gz C of the listed projectors
-  T* qs = q + (size_t)P * AROWS;           // [P][AROWS]: gy gz (C - C')
-  int* list = reinterpret_cast<int*>(qs + (size_t)P * AROWS);
-  __shared__ int wcount[PNT / 32];
-  const int i = blockIdx.z, z = blockIdx.y, y0 = blockIdx.x * AROWS;
-  const int slot = nl_slot(a);
-  const double* C = a.C[slot] + (i64)i * P;
-  const double* Cp = a.nls ? a.C[a.st->cur] + (i64)i * P : nullptr;  // the trial's previous iterate
+// Projectors of one tile (plane z, rows [y0, y0 + ry), columns [x0, x0 + rx)),
+// listed in index order (ballot and prefix counts).  Returns the count.
+__device__ __forceinline__ int list_tile(const NlTables& t, int z, int y0, int ry, int x0, int rx, int* list,
+                                         int* wcount) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // projectors whose z window holds this plane and whose y window meets the rows
   bool take = false;
-  if (tid < P) {
+  if (tid < t.P) {
     const int* w = t.win + tid * 6;
-    const int dz = (z - w[4] + nz) % nz;
-    const int dy = (y0 - w[2] + ny) % ny;  // rows y0 .. y0 + AROWS - 1 meet [w2, w2 + w3) (mod ny)
-    const int rows = min(AROWS, ny - y0);
-    take = dz < w[5] && (dy < w[3] || dy + rows > ny || w[3] >= ny);
-    if (!take && dz < w[5]) {
-      for (int r = 0; r < rows && !take; ++r) take = ((y0 + r - w[2] + ny) % ny) < w[3];
-    }
+    take = meets(z, 1, w[4], w[5], t.nz) && meets(y0, ry, w[2], w[3], t.ny) && meets(x0, rx, w[0], w[1], t.nx);
   }
   const unsigned m = __ballot_sync(0xffffffffu, take);
   if (lane == 0) wcount[warp] = __popc(m);
@@ -134,49 +83,167 @@ __global__ void __launch_bounds__(PNT) k_nl_apply(NlArgs<T> a) {
   }
   if (take) list[off + __popc(m & ((1u << lane) - 1u))] = tid;
   __syncthreads();
-  for (int e = tid; e < cnt * AROWS; e += PNT) {
-    const int k = e / AROWS, r = e - k * AROWS;
-    const int p = list[k], y = y0 + r;
+  return cnt;
+}
+
+// Projections, first stage: for one plane and PROWS rows of one orbital,
+// sum_y gy_p[y] sum_x gx_p[x] w[y][x] for every projector (zero for those not
+// listed), into part[i][z][row block][p].  The rows are staged in shared
+// memory; each (projector, row) pair's dot product runs over the x window.
+template <typename T>
+__global__ void __launch_bounds__(PNT) k_nl_project(NlArgs<T> a, double* part) {
+  if (a.st && (a.st->done || !gate_open(a.st, a.gate))) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const NlTables& t = a.tab;
+  const int nx = t.nx, ny = t.ny, nz = t.nz, P = t.P;
+  T* ws = reinterpret_cast<T*>(smem_raw);          // [PROWS][nx]
+  T* rs = ws + (size_t)PROWS * nx;                 // [P][PROWS] row sums of the listed projectors
+  int* list = reinterpret_cast<int*>(rs + (size_t)P * PROWS);
+  __shared__ int wcount[PNT / 32];
+  const int nyb = (ny + PROWS - 1) / PROWS;
+  const int yb = blockIdx.x, z = blockIdx.y, i = blockIdx.z;
+  const int y0 = yb * PROWS, ry = min(PROWS, ny - y0);
+  const int slot = nl_slot(a);
+  const T* x = a.X[slot] + (i64)i * nx * ny * nz + (i64)z * nx * ny + (i64)y0 * nx;
+  for (int e = threadIdx.x; e < ry * nx; e += PNT) ws[e] = x[e];
+  const int cnt = list_tile(t, z, y0, ry, 0, nx, list, wcount);
+  for (int e = threadIdx.x; e < cnt * PROWS; e += PNT) {
+    const int k = e / PROWS, r = e - k * PROWS;
+    T acc = T(0);
+    if (r < ry) {
+      const int p = list[k];
+      const int* w = t.win + p * 6;
+      const T* gxp = tab_x<T>(t, p);
+      const T* row = ws + (size_t)r * nx;
+      int xx = w[0];
+      for (int kx = 0; kx < w[1]; ++kx) {
+        acc += gxp[xx] * row[xx];
+        if (++xx == nx) xx = 0;
+      }
+    }
+    rs[e] = acc;
+  }
+  __syncthreads();
+  double* out = part + (((i64)i * nz + z) * nyb + yb) * P;
+  for (int p = threadIdx.x; p < P; p += PNT) out[p] = 0.0;
+  __syncthreads();
+  for (int k = threadIdx.x; k < cnt; k += PNT) {
+    const int p = list[k];
+    double v = 0.0;
+    for (int r = 0; r < ry; ++r) v += (double)(tab_y<T>(t, p, y0 + r) * rs[k * PROWS + r]);
+    out[p] = v;
+  }
+}
+
+// Projections, second stage: C_ip = dV sum_z gz_p[z] sum_blocks part, in a fixed order.
+template <typename T>
+__global__ void __launch_bounds__(PNT) k_nl_reduce(NlArgs<T> a, const double* part) {
+  if (a.st && (a.st->done || !gate_open(a.st, a.gate))) return;
+  const NlTables& t = a.tab;
+  const int i = blockIdx.x, P = t.P, nz = t.nz;
+  const int nyb = (t.ny + PROWS - 1) / PROWS;
+  const int slot = nl_slot(a);
+  for (int p = threadIdx.x; p < P; p += PNT) {
+    double c = 0.0;
+    for (int z = 0; z < nz; ++z) {
+      double sz = 0.0;
+      for (int b = 0; b < nyb; ++b) sz += part[(((i64)i * nz + z) * nyb + b) * P + p];
+      c += t.gz[(i64)p * nz + z] * sz;
+    }
+    a.C[slot][(i64)i * P + p] = a.dV * c;
+  }
+}
+
+// NL_i = sum_p xi_p C_ip (and NLS_i with C - C') on a tile of ATY rows x ATX
+// columns of one plane: the listed projectors' column tables and row
+// coefficients are staged in shared memory; each thread forms 4 columns of
+// one row.
+template <typename T>
+__global__ void __launch_bounds__(PNT) k_nl_apply(NlArgs<T> a) {
+  if (a.st && (a.st->done || !gate_open(a.st, a.gate))) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const NlTables& t = a.tab;
+  const int nx = t.nx, ny = t.ny, nz = t.nz, P = t.P;
+  T* gxs = reinterpret_cast<T*>(smem_raw);  // [P][ATX]
+  T* q = gxs + (size_t)P * ATX;              // [P][ATY]: gy gz C
+  T* qs = q + (size_t)P * ATY;               // [P][ATY]: gy gz (C - C')
+  int* list = reinterpret_cast<int*>(qs + (size_t)P * ATY);
+  __shared__ int wcount[PNT / 32];
+  const int ntx = (nx + ATX - 1) / ATX;
+  const int x0 = (blockIdx.x % ntx) * ATX, y0 = (blockIdx.x / ntx) * ATY;
+  const int z = blockIdx.y, i = blockIdx.z;
+  const int rx = min(ATX, nx - x0), ry = min(ATY, ny - y0);
+  const int slot = nl_slot(a);
+  const double* C = a.C[slot] + (i64)i * P;
+  const double* Cp = a.nls ? a.C[a.st->cur] + (i64)i * P : nullptr;  // the trial's previous iterate
+  const int cnt = list_tile(t, z, y0, ry, x0, rx, list, wcount);
+  for (int e = threadIdx.x; e < cnt * ATX; e += PNT) {
+    const int k = e / ATX, c = e - k * ATX;
+    gxs[e] = c < rx ? tab_x<T>(t, list[k])[x0 + c] : T(0);
+  }
+  for (int e = threadIdx.x; e < cnt * ATY; e += PNT) {
+    const int k = e / ATY, r = e - k * ATY;
+    const int p = list[k];
     T g = T(0);
-    if (y < ny) g = tab_y<T>(t, p, y) * tab_z<T>(t, p, z);
+    if (r < ry) g = tab_y<T>(t, p, y0 + r) * tab_z<T>(t, p, z);
     q[e] = g * (T)C[p];
     qs[e] = Cp ? g * (T)(C[p] - Cp[p]) : T(0);
   }
   __syncthreads();
-  const i64 base = (i64)i * nx * ny * nz + (i64)z * nx * ny;
-  const int rows = min(AROWS, ny - y0);
-  for (int e = tid; e < nx * rows; e += PNT) {
-    const int r = e / nx, xx = e - r * nx, y = y0 + r;
-    T v = T(0), vs = T(0);
-    for (int k = 0; k < cnt; ++k) {
-      const T g = tab_x<T>(t, list[k])[xx];
-      v += g * q[k * AROWS + r];
-      vs += g * qs[k * AROWS + r];
+  const int tx = threadIdx.x % (ATX / 4), r = threadIdx.x / (ATX / 4);
+  T v[4] = {0, 0, 0, 0}, vs[4] = {0, 0, 0, 0};
+  for (int k = 0; k < cnt; ++k) {
+    const T qk = q[k * ATY + r], qsk = qs[k * ATY + r];
+    const T* g = gxs + k * ATX + 4 * tx;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      v[j] += g[j] * qk;
+      vs[j] += g[j] * qsk;
     }
-    const i64 o = base + (i64)y * nx + xx;
-    a.nl[o] = v;
-    if (a.nls) a.nls[o] = vs;
+  }
+  if (r < ry) {
+    const i64 o = (i64)i * nx * ny * nz + (i64)z * nx * ny + (i64)(y0 + r) * nx + x0 + 4 * tx;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (4 * tx + j < rx) {
+        a.nl[o + j] = v[j];
+        if (a.nls) a.nls[o + j] = vs[j];
+      }
+    }
   }
 }
 
 template <typename T>
 size_t nl_apply_smem(int P) {
-  return (size_t)2 * P * AROWS * sizeof(T) + (size_t)P * sizeof(int);
+  return (size_t)P * (ATX + 2 * ATY) * sizeof(T) + (size_t)P * sizeof(int);
+}
+template <typename T>
+size_t nl_project_smem(int P, int nx) {
+  return (size_t)(PROWS * nx + P * PROWS) * sizeof(T) + (size_t)P * sizeof(int);
 }
 
 }  // namespace
 
 template <typename T>
-void launch_nl_project(const NlArgs<T>& a, cudaStream_t s) {
+void launch_nl_project(const NlArgs<T>& a, double* part, cudaStream_t s) {
+  const int nyb = (a.tab.ny + PROWS - 1) / PROWS;
   prof_begin("nl_project", s);
-  k_nl_project<T><<<dim3(a.tab.P, a.N), PNT, 0, s>>>(a);
+  k_nl_project<T><<<dim3(nyb, a.tab.nz, a.N), PNT, nl_project_smem<T>(a.tab.P, a.tab.nx), s>>>(a, part);
+  prof_end(s);
+  prof_begin("nl_reduce", s);
+  k_nl_reduce<T><<<a.N, PNT, 0, s>>>(a, part);
   prof_end(s);
 }
 template <typename T>
 void launch_nl_apply(const NlArgs<T>& a, cudaStream_t s) {
+  const int tiles = ((a.tab.nx + ATX - 1) / ATX) * ((a.tab.ny + ATY - 1) / ATY);
   prof_begin("nl_apply", s);
-  k_nl_apply<T><<<dim3((a.tab.ny + AROWS - 1) / AROWS, a.tab.nz, a.N), PNT, nl_apply_smem<T>(a.tab.P), s>>>(a);
+  k_nl_apply<T><<<dim3(tiles, a.tab.nz, a.N), PNT, nl_apply_smem<T>(a.tab.P), s>>>(a);
   prof_end(s);
+}
+
+size_t nl_part_bytes(int N, int P, const int n[3]) {
+  return sizeof(double) * (size_t)N * n[2] * ((n[1] + PROWS - 1) / PROWS) * P;
 }
 
 void configure_nonlocal() {
@@ -184,9 +251,14 @@ void configure_nonlocal() {
                        (int)nl_apply_smem<float>(kMaxProj));
   cudaFuncSetAttribute(k_nl_apply<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)nl_apply_smem<double>(kMaxProj));
+  cudaFuncSetAttribute(k_nl_project<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)nl_project_smem<float>(kMaxProj, kMaxProjGrid));
+  cudaFuncSetAttribute(k_nl_project<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)nl_project_smem<double>(kMaxProj, kMaxProjGrid));
 }
-template void launch_nl_project<float>(const NlArgs<float>&, cudaStream_t);
-template void launch_nl_project<double>(const NlArgs<double>&, cudaStream_t);
+
+template void launch_nl_project<float>(const NlArgs<float>&, double*, cudaStream_t);
+template void launch_nl_project<double>(const NlArgs<double>&, double*, cudaStream_t);
 template void launch_nl_apply<float>(const NlArgs<float>&, cudaStream_t);
 template void launch_nl_apply<double>(const NlArgs<double>&, cudaStream_t);
 

@@ -91,6 +91,7 @@ struct CtxProfiler : ProfRecorder {
 struct pou_ctx {
   pou_config cfg;
   int dt;       // 0 double, 1 float
+  int tf32_single;  // POU_FP32_TF32: the tensor-core Gram takes one TF32 product
   size_t esz;   // bytes per orbital element
   int nx, ny, nz, N;
   i64 ng;
@@ -145,6 +146,7 @@ struct pou_ctx {
   double* nlCe;
   void* nl;
   void* nls;
+  double* nl_part;  // per-plane partial projections
   State* st;
   double* hist_E;
   double* hist_tau;
@@ -282,7 +284,7 @@ void enqueue_nonlocal(pou_ctx* c, int sel, const T* explicit_block, int gate, Ap
   n.gate = gate;
   n.N = c->N;
   n.dV = c->dV;
-  launch_nl_project<T>(n, c->stream);
+  launch_nl_project<T>(n, c->nl_part, c->stream);
   launch_nl_apply<T>(n, c->stream);
   aa->nl = tp<T>(c->nl);
   aa->nls = n.nls;
@@ -308,6 +310,7 @@ void enqueue_second_orth(pou_ctx* c, int soft_limit) {
   g.ng = c->ng;
   g.N = c->N;
   g.split = c->split;
+  g.tf32_single = c->tf32_single;
   launch_gram<T>(g, s);
   int nsplit, npair;
   i64 chunk;
@@ -358,6 +361,7 @@ void enqueue_diag(pou_ctx* c) {
   g.ng = c->ng;
   g.N = c->N;
   g.split = c->split;
+  g.tf32_single = c->tf32_single;
   launch_gram<T>(g, s);
   int nsplit, npair;
   i64 chunk;
@@ -446,6 +450,7 @@ void enqueue_direction_full(pou_ctx* c) {
   g.ng = c->ng;
   g.N = c->N;
   g.split = c->split;
+  g.tf32_single = c->tf32_single;
   launch_gram<T>(g, s);
   int nsplit, npair;
   i64 chunk;
@@ -579,6 +584,7 @@ void enqueue_pass(pou_ctx* c) {
   g.ng = c->ng;
   g.N = c->N;
   g.split = c->split;
+  g.tf32_single = c->tf32_single;
   launch_gram<T>(g, s);
   int nsplit, npair;
   i64 chunk;
@@ -715,6 +721,7 @@ pou_status init_from_staged(pou_ctx* c) {
   g.ng = c->ng;
   g.N = c->N;
   g.split = c->split;
+  g.tf32_single = c->tf32_single;
   launch_gram<T>(g, s);
   int nsplit, npair;
   i64 chunk;
@@ -1069,7 +1076,8 @@ pou_status pou_create(const pou_config* cfg, pou_ctx** out) {
   }
   if (cfg->stencil_order != 2 && cfg->stencil_order != 4) return POU_EINVAL;
   if (cfg->N < 1 || cfg->N > POU_MAX_N) return POU_EINVAL;
-  if (cfg->precision != POU_FP64 && cfg->precision != POU_FP32) return POU_EINVAL;
+  if (cfg->precision != POU_FP64 && cfg->precision != POU_FP32 && cfg->precision != POU_FP32_TF32)
+    return POU_EINVAL;
   if (cfg->bb_variant < 1 || cfg->bb_variant > 3) return POU_EINVAL;
   if (!(cfg->delta > 0.0 && cfg->delta < 1.0) || !(cfg->eta >= 0.0 && cfg->eta <= 1.0)) return POU_EINVAL;
   if (!(cfg->rho1 >= 0.0) || cfg->max_backtrack < 0 || cfg->max_backtrack > 60) return POU_EINVAL;
@@ -1093,6 +1101,7 @@ pou_status pou_create(const pou_config* cfg, pou_ctx** out) {
   pou_ctx* c = new pou_ctx();  // value-initialised: every pointer starts null
   c->cfg = *cfg;
   c->dt = cfg->precision == POU_FP64 ? 0 : 1;
+  c->tf32_single = cfg->precision == POU_FP32_TF32 ? 1 : 0;
   c->esz = c->dt == 0 ? 8 : 4;
   c->nx = cfg->n[0];
   c->ny = cfg->n[1];
@@ -1214,7 +1223,7 @@ void pou_destroy(pou_ctx* c) {
                   c->dR, c->dZ, c->tabs.gx, c->fpart, c->ublock, c->gblock, c->rho_e, c->V64_e, c->rimg,
                   c->Z[0], c->Z[1], c->dir_opart, c->dir_bpart, c->dir_dpart, c->zero_sigma,
                   c->tfac, c->D[0], c->D[1], c->Zs[0], c->Zs[1], c->cg_opart, c->cg_coef,
-                  c->nl_mem, c->nlC[0], c->nlC[1], c->nlCe, c->nl, c->nls};
+                  c->nl_mem, c->nlC[0], c->nlC[1], c->nlCe, c->nl, c->nls, c->nl_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->dt == 1) {
@@ -1292,6 +1301,8 @@ pou_status pou_set_projectors(pou_ctx* c, int P, const double* centres, const do
   if (!c) return POU_EINVAL;
   if (P < 0 || P > POU_MAX_PROJ) return fail(c, POU_EINVAL, "need 0 <= P <= %d projectors", POU_MAX_PROJ);
   if (P > 0 && (!centres || !widths || !amps)) return fail(c, POU_EINVAL, "null projector arrays");
+  if (P > 0 && c->nx > kMaxProjGrid)
+    return fail(c, POU_EINVAL, "projectors need nx <= %d", kMaxProjGrid);
   if (P > 0 && c->cfg.solver == 1)
     return fail(c, POU_EINVAL, "projectors are not combined with the conjugate-gradient solver");
   for (int p = 0; p < P; ++p) {
@@ -1306,10 +1317,11 @@ pou_status pou_set_projectors(pou_ctx* c, int P, const double* centres, const do
     cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
   }
-  void* old[] = {c->nl_mem, c->nlC[0], c->nlC[1], c->nlCe, c->nl, c->nls};
+  void* old[] = {c->nl_mem, c->nlC[0], c->nlC[1], c->nlCe, c->nl, c->nls, c->nl_part};
   for (void* q : old)
     if (q) cudaFree(q);
   c->nl_mem = c->nl = c->nls = nullptr;
+  c->nl_part = nullptr;
   c->nlC[0] = c->nlC[1] = c->nlCe = nullptr;
   c->P = 0;
   c->nlt = NlTables{};
@@ -1376,6 +1388,7 @@ pou_status pou_set_projectors(pou_ctx* c, int P, const double* centres, const do
   DALLOC(c->nlCe, (size_t)c->N * P * sizeof(double));
   DALLOC(c->nl, blk);
   DALLOC(c->nls, blk);
+  DALLOC(c->nl_part, nl_part_bytes(c->N, P, n));
   c->nlt.P = P;
   c->nlt.nx = c->nx;
   c->nlt.ny = c->ny;
@@ -1550,6 +1563,7 @@ pou_status gradient_norm_impl(pou_ctx* c, int cur, double* out) {
   g.ng = c->ng;
   g.N = c->N;
   g.split = c->split;
+  g.tf32_single = c->tf32_single;
   launch_gram<T>(g, s);
   int nsplit, npair;
   i64 chunk;

@@ -113,6 +113,7 @@ struct GramArgs {
   int N;
   double* split;        // [nsplit][npair][ST*ST]
   const double* tfac;   // trial mode: orbital i steps tau_trial * tfac[i] (nullptr: 1 for all)
+  int tf32_single;      // FP32 tensor-core Gram: one TF32 product (hi hi) instead of the three split ones
 };
 template <typename T>
 int gram_supertile();
@@ -285,8 +286,11 @@ struct NlArgs {
   int N;
   double dV;
 };
+constexpr int kMaxProjGrid = 512;  // largest nx the projection kernel stages (fits shared memory)
+// part: scratch of nl_part_bytes(N, P, n) bytes (per-plane partial sums)
+size_t nl_part_bytes(int N, int P, const int n[3]);
 template <typename T>
-void launch_nl_project(const NlArgs<T>& a, cudaStream_t s);
+void launch_nl_project(const NlArgs<T>& a, double* part, cudaStream_t s);
 template <typename T>
 void launch_nl_apply(const NlArgs<T>& a, cudaStream_t s);
 void configure_nonlocal();

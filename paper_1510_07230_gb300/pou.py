@@ -25,7 +25,7 @@ _lib = C.CDLL(LIB_PATH)
 OK, EINVAL, ENOMEM, ECUDA, ENOTSPD, ENAN, ENOCONV = range(7)
 STATUS_NAMES = {0: "POU_OK", 1: "POU_EINVAL", 2: "POU_ENOMEM", 3: "POU_ECUDA", 4: "POU_ENOTSPD",
                 5: "POU_ENAN", 6: "POU_ENOCONV"}
-FP64, FP32 = 0, 1
+FP64, FP32, FP32_TF32 = 0, 1, 2  # FP32 = TF32x3 split products; FP32_TF32 = single-product TF32 Gram
 OPT_PAR, OPTM_QR = 0, 1  # config direction: per-orbital sigma_ii (the paper's method) or full Sigma
 TAU_SHARED, TAU_PER_ORBITAL = 0, 1  # config tau_mode
 STEEPEST_DESCENT, CONJUGATE_GRADIENT = 0, 1  # config solver

@@ -915,3 +915,30 @@ def test_device_orbitals_and_stream(P):
     assert s.launch_count() > 10 * 7
     s.close()
     s2.close()
+
+
+def test_single_product_tf32_gram_form(P):
+    """POU_FP32_TF32 (one TF32 product in the iteration's Gram matrices) in
+    the bench's kernel configuration: the first steps follow the oracle, the
+    returned orbitals are orthonormal to the Gram's averaged rounding and carry
+    the reported energy."""
+    n, L, N = 40, 16.0, 128
+    R, Z = inputs.atoms(71, 32, L, "uniform26")
+    U = inputs.random_orbitals(71, N, (n, n, n)).astype(np.float32)
+    cfg = ocfg(n, L, N, order=4)
+    vext = O.vext_gaussians(cfg, R, Z, 0.8)
+    s = solver(P, n, L, N, order=4, precision=P.FP32_TF32)
+    s.set_atoms(R, Z, 0.8)
+    s.set_orbitals(U)
+    steps = 8
+    s.iterate(steps)
+    Eg, _ = s.history()
+    st = O.run(U.astype(np.float64), vext, cfg, steps)
+    Eo = np.array([h.energy for h in st.history])
+    np.testing.assert_allclose(Eg[:steps], Eo[:steps], rtol=1e-5)
+    W = s.get_orbitals().astype(np.float64)
+    ortho = np.max(np.abs(O.inner_matrix(W, W, cfg) - np.eye(N)))
+    assert ortho < 2e-5, ortho
+    e = s.energy()["total"]
+    assert abs(O.energy(W, vext, cfg) - e) <= 1e-6 * abs(e)
+    s.close()
