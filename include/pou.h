@@ -245,6 +245,15 @@ pou_status pou_get_history(pou_ctx* ctx, double* E, double* tau, int max_entries
 pou_status pou_get_state(pou_ctx* ctx, void* blob, size_t* size);
 pou_status pou_set_state(pou_ctx* ctx, const void* blob, size_t size);
 
+/* Diagnostics (no counterpart in the paper): every wait of the tensor-core
+ * kernels on a shared-memory barrier gives up after a time limit, records it
+ * and lets the kernel return, so that a lost arrival surfaces as POU_ECUDA
+ * instead of a hang.  This runs that bounded wait on a barrier that nothing
+ * arrives at, with limit_s seconds (0 < limit_s <= 10), on the current device
+ * and its legacy default stream; *timed_out = 1 when it gave up as designed.
+ * POU_ECUDA if the launch failed; the device stays usable either way. */
+pou_status pou_selftest_wait_timeout(double limit_s, int* timed_out);
+
 /* Block until all work queued by the context has finished. */
 pou_status pou_synchronize(pou_ctx* ctx);
 

@@ -477,3 +477,43 @@ void launch_gram_tc(const GramArgs<float>& a, int nsplit, cudaStream_t s) {
 }
 
 }  // namespace pou
+
+namespace pou {
+namespace {
+// Self-test of the bounded barrier wait every tensor-core kernel relies on:
+// one thread waits on an mbarrier that expects one arrival and gets none, so
+// the wait gives up after limit_ns and records it; no tensor memory is held
+// and nothing else waits.
+__global__ void k_wait_selftest(uint64_t limit_ns, int* out) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ volatile int abort_flag;
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    const uint32_t b = tc::smem_u32(&bar);
+    tc::mbar_init(b, 1);
+    tc::mbar_init_fence();
+    const bool ok = tc::mbar_wait(b, 0, &abort_flag, limit_ns);
+    out[0] = ok ? 0 : 1;
+    out[1] = abort_flag;
+  }
+}
+}  // namespace
+
+int wait_selftest(double limit_s, int* timed_out) {
+  int* d = nullptr;
+  if (cudaMalloc(&d, 2 * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return 2;
+  }
+  const uint64_t ns = (uint64_t)(limit_s * 1e9);
+  k_wait_selftest<<<1, 32>>>(ns, d);
+  int h[2] = {0, 0};
+  const cudaError_t e1 = cudaGetLastError();
+  const cudaError_t e2 = cudaMemcpy(h, d, sizeof h, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e1 != cudaSuccess || e2 != cudaSuccess) return 3;
+  *timed_out = (h[0] == 1 && h[1] == 1) ? 1 : 0;
+  return 0;
+}
+
+}  // namespace pou

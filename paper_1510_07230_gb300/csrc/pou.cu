@@ -1836,6 +1836,12 @@ pou_status pou_set_state(pou_ctx* c, const void* blob, size_t size) {
   return POU_OK;
 }
 
+pou_status pou_selftest_wait_timeout(double limit_s, int* timed_out) {
+  if (!timed_out || !(limit_s > 0.0) || limit_s > 10.0) return POU_EINVAL;
+  *timed_out = 0;
+  return wait_selftest(limit_s, timed_out) == 0 ? POU_OK : POU_ECUDA;
+}
+
 pou_status pou_synchronize(pou_ctx* c) {
   if (!c) return POU_EINVAL;
   CK(cudaStreamSynchronize(c->stream));

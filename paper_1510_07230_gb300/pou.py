@@ -93,6 +93,7 @@ _SIG = {
     "pou_get_state": (_I, [_P, _P, C.POINTER(C.c_size_t)]),
     "pou_set_state": (_I, [_P, _P, C.c_size_t]),
     "pou_synchronize": (_I, [_P]),
+    "pou_selftest_wait_timeout": (_I, [_D, C.POINTER(C.c_int)]),
     "pou_launch_count": (C.c_longlong, [_P]),
     "pou_set_profiling": (_I, [_P, _I]),
     "pou_get_profile": (_I, [_P, _I, _P, _P, _P, C.POINTER(C.c_int)]),
@@ -452,3 +453,13 @@ def hartree(n, L, rho, vh, workspace, stream=None):
                           _stream_ptr(stream))
     if st != OK:
         raise PouError(st, "pou_hartree")
+
+
+def selftest_wait_timeout(limit_s=0.05) -> bool:
+    """Run the bounded barrier wait on a barrier nothing arrives at
+    (pou_selftest_wait_timeout); True when it gave up as designed."""
+    t = C.c_int(0)
+    st = _lib.pou_selftest_wait_timeout(float(limit_s), C.byref(t))
+    if st != OK:
+        raise PouError(st, "pou_selftest_wait_timeout")
+    return bool(t.value)

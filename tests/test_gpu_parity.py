@@ -942,3 +942,22 @@ def test_single_product_tf32_gram_form(P):
     e = s.energy()["total"]
     assert abs(O.energy(W, vext, cfg) - e) <= 1e-6 * abs(e)
     s.close()
+
+
+def test_bounded_barrier_wait_gives_up_and_the_device_stays_usable(P):
+    """A tensor-core kernel's barrier wait on an arrival that never comes
+    gives up after its limit and reports it (no hang, no trap); the next
+    tensor-core Gram on the same device is correct."""
+    import time
+    t0 = time.time()
+    assert P.selftest_wait_timeout(0.05)
+    assert time.time() - t0 < 30.0
+    rng = np.random.default_rng(4)
+    A = torch.as_tensor(rng.standard_normal((64, 5000)), dtype=torch.float32, device="cuda")
+    S = torch.empty((64, 64), dtype=torch.float64, device="cuda")
+    ws = torch.empty(P.gram_workspace_bytes(P.DT_F32, 5000, 64) // 8 + 1, dtype=torch.float64, device="cuda")
+    P.gram(A, 0.5, S, ws)
+    Ar = A.double().cpu().numpy()
+    ref = 0.5 * (Ar @ Ar.T)
+    d = np.sum(Ar * Ar, 1)
+    assert np.max(np.abs(S.cpu().numpy() - ref) / (0.5 * np.sqrt(np.outer(d, d)))) < 2e-6
