@@ -120,7 +120,7 @@ typedef struct {
                          tau_mode = 0, n_org = 1, n_diag = 0, and four more orbital blocks */
 } pou_config;
 
-#define POU_MAX_N 512      /* FP32 form (without the subspace diagonalisation) */
+#define POU_MAX_N 512      /* FP32 forms (without the subspace diagonalisation) */
 #define POU_MAX_N_FP64 128 /* FP64 form, the subspace diagonalisation, FP64 pou_rotate */
 
 typedef struct {

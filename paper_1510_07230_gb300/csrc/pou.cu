@@ -1093,8 +1093,8 @@ pou_status pou_create(const pou_config* cfg, pou_ctx** out) {
       (cfg->direction != 0 || cfg->n_org != 1 || cfg->n_diag != 0))
     return POU_EINVAL;
   if (cfg->tau_mode == 1 && cfg->solver == 1) return POU_EINVAL;  // CG takes its own per-orbital steps
-  // N > 128: FP32 form only, without the subspace diagonalisation
-  if (cfg->N > POU_MAX_N_FP64 && (cfg->precision != POU_FP32 || cfg->n_diag > 0)) return POU_EINVAL;
+  // N > 128: the FP32 forms only (split or single TF32 Gram), without the subspace diagonalisation
+  if (cfg->N > POU_MAX_N_FP64 && (cfg->precision == POU_FP64 || cfg->n_diag > 0)) return POU_EINVAL;
   const long long ng = (long long)cfg->n[0] * cfg->n[1] * cfg->n[2];
   if ((long long)cfg->N > ng) return POU_EINVAL;
 
