@@ -285,11 +285,38 @@ def test_iteration_large_n_fp32(P):
     s.close()
 
 
+def test_iteration_large_n_single_tf32(P):
+    """POU_FP32_TF32 with N = 192 (two 128-row blocks: the single TF32
+    product on the diagonal and the off-diagonal block pairs of the
+    tensor-core Gram): the first steps follow the FP64 oracle to the form's
+    averaged rounding, the orbitals stay orthonormal to it and carry the
+    reported energy."""
+    N = 192
+    n, L, R, Z, U = _large_n_system(N)
+    cfg = ocfg(n, L, N)
+    vext = O.vext_gaussians(cfg, R, Z, 0.8)
+    s = solver(P, n, L, N, precision=P.FP32_TF32)
+    s.set_atoms(R, Z, 0.8)
+    s.set_orbitals(U.astype(np.float32))
+    s.iterate(6)
+    Eg, _ = s.history()
+    st = O.run(U.astype(np.float32).astype(np.float64), vext, cfg, 6)
+    Eo = np.array([h.energy for h in st.history])
+    np.testing.assert_allclose(Eg[:len(Eo)], Eo[:len(Eg)], rtol=1e-5)
+    W = s.get_orbitals().astype(np.float64)
+    assert np.max(np.abs(O.inner_matrix(W, W, cfg) - np.eye(N))) < 2e-5
+    e = s.energy()["total"]
+    assert abs(O.energy(W, vext, cfg) - e) <= 1e-6 * abs(e)
+    s.close()
+
+
 def test_large_n_fp64_form_is_einval(P):
     with pytest.raises(P.PouError):
         solver(P, (16, 16, 18), (6.0, 6.0, 7.0), 192, precision=0)
     with pytest.raises(P.PouError):
         solver(P, (16, 16, 18), (6.0, 6.0, 7.0), 192, precision=1, n_diag=50)
+    with pytest.raises(P.PouError):
+        solver(P, (16, 16, 18), (6.0, 6.0, 7.0), 192, precision=2, n_diag=50)
 
 
 def test_full_size_160_energy_and_h_apply(P):
@@ -318,18 +345,23 @@ def test_full_size_160_energy_and_h_apply(P):
     s.close()
 
 
-def test_bench_kernel_configuration_mixed_n128_13pt(P):
+@pytest.mark.parametrize("n,L", [((40, 40, 40), (16.0, 16.0, 16.0)), ((64, 64, 32), (24.0, 24.0, 12.0))])
+def test_bench_kernel_configuration_mixed_n128_13pt(P, n, L):
     """The launch configuration the bench times (mixed form, N = 128, 13-point
     stencil: the tensor-core trial Gram over one 128 x 128 block, the
     tensor-core rotation with all four 32-orbital atoms of R^-1, the one-CTA
-    Cholesky) on a 40^3 grid the oracle steps through in seconds.  The first
-    steps follow the FP64 oracle's trajectory from the same FP32-rounded
-    start; at least one of them takes the second Cholesky-QR pass; the
-    returned orbitals are orthonormal, and the energy, density and residual
-    norm the library reports are those the oracle computes from them."""
-    n, L, N = 40, 16.0, 128
-    R, Z = inputs.atoms(71, 32, L, "uniform26")
-    U = inputs.random_orbitals(71, N, (n, n, n)).astype(np.float32)
+    Cholesky) on grids the oracle steps through in seconds, with equal
+    spacings in the three directions as on the 160^3 workload (one kinetic
+    sum): 64 x 64 x 32 tiles exactly like 160^3 (whole 32 x 16 tiles), 40^3
+    leaves ragged tiles.  The first steps follow the FP64 oracle's
+    trajectory from the same FP32-rounded start (on 40^3 at least one of them
+    takes the second Cholesky-QR pass); the returned orbitals are
+    orthonormal, and the energy, density and residual norm the library
+    reports are those the oracle computes from them."""
+    N = 128
+    R, Z = inputs.atoms(71, 32, L[0], "uniform26")
+    R[:, 2] *= L[2] / L[0]
+    U = inputs.random_orbitals(71, N, n).astype(np.float32)
     cfg = ocfg(n, L, N, order=4)
     vext = O.vext_gaussians(cfg, R, Z, 0.8)
     s = solver(P, n, L, N, order=4, precision=1)
@@ -338,7 +370,8 @@ def test_bench_kernel_configuration_mixed_n128_13pt(P):
     steps = 8
     rep = s.iterate(steps)
     assert rep["iterations"] == steps
-    assert rep["second_passes"] >= 1
+    if n[0] == 40:
+        assert rep["second_passes"] >= 1
     Eg, _ = s.history()
     st = O.run(U.astype(np.float64), vext, cfg, steps)
     Eo = np.array([h.energy for h in st.history])
@@ -354,6 +387,31 @@ def test_bench_kernel_configuration_mixed_n128_13pt(P):
     HW = O.apply_h(W, O.total_potential(O.density(W), vext, cfg), cfg)
     g_ref = O.gradient_residual(W, HW, cfg)
     assert abs(s.gradient_norm() - g_ref) <= 3e-3 * g_ref + 2e-5
+    s.close()
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_mixed_trajectory_non_cubic_grid(P, order):
+    """The mixed form on a grid with three different spacings (the FP32
+    H-apply keeps per-axis kinetic sums, the step's Barzilai-Borwein terms
+    included): the first steps follow the oracle."""
+    n, L, N = (64, 32, 16), (12.0, 7.0, 3.5), 8
+    R, Z, U = _system(n, L, N, 21, M=3)
+    U = U.astype(np.float32)
+    cfg = ocfg(n, L, N, order=order)
+    vext = O.vext_gaussians(cfg, R, Z, 0.8)
+    s = solver(P, n, L, N, order=order, precision=1)
+    s.set_atoms(R, Z, 0.8)
+    s.set_orbitals(U)
+    steps = 8
+    s.iterate(steps)
+    Eg, tg = s.history()
+    st = O.run(U.astype(np.float64), vext, cfg, steps)
+    Eo = np.array([h.energy for h in st.history])
+    np.testing.assert_allclose(Eg[:steps], Eo[:steps], rtol=2e-6)
+    W = s.get_orbitals().astype(np.float64)
+    e = s.energy()["total"]
+    assert abs(O.energy(W, vext, cfg) - e) <= 1e-7 * abs(e)
     s.close()
 
 
@@ -462,9 +520,12 @@ def test_evaluate_energy_terms(P, precision, order):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("order,n", [(2, (20, 12, 10)), (4, (20, 12, 10)), (4, (5, 6, 8)), (2, (27, 9, 4))])
+@pytest.mark.parametrize("order,n", [(2, (20, 12, 10)), (4, (20, 12, 10)), (4, (5, 6, 8)), (2, (27, 9, 4)),
+                                     (4, (64, 32, 12)), (2, (32, 48, 5)), (4, (32, 16, 3))])
 def test_apply_h_through_adjoint(P, precision, order, n):
-    """a1: HW = -1/2 Lap_h W + V W, read through dE/dU = 2 f dV H U with g = 1/(2 f dV)."""
+    """a1: HW = -1/2 Lap_h W + V W, read through dE/dU = 2 f dV H U with g = 1/(2 f dV).
+    The grids cover whole and ragged 32 x 16 tiles of the FP32 kernel, odd
+    nx (the scalar kernel) and fewer planes than the stencil's reach in z."""
     L, N = (6.0, 5.0, 4.0), 2
     R, Z, U = _system(n, L, N, 9)
     if precision == 1:
