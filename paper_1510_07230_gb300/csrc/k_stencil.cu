@@ -67,6 +67,11 @@ template <int N>
 __device__ __forceinline__ void cp_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
+// 16-byte copy through L2 only (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16_cg(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
 
 template <typename T, int R>
 struct Stage {
@@ -618,7 +623,9 @@ constexpr int TXP = 16;         // threads per tile row
 constexpr int TYP = 16;         // tile rows
 constexpr int NTP = TXP * TYP;  // threads per CTA
 constexpr int PW = 2 * TXP;     // points per tile row
-constexpr int ROW = PW + 4;     // shared row: two halo cells each side
+constexpr int CX0 = 4;          // first centre column of a shared row
+constexpr int ROW = PW + 2 * CX0;  // shared row: a 16-byte halo chunk each side
+constexpr int CH = PW / 4;      // 16-byte chunks per tile row
 constexpr int PFP = 2;          // planes in flight
 
 template <int R, bool HIST, bool NLT>
@@ -731,23 +738,37 @@ __global__ void __launch_bounds__(NTP, (CUBIC && !NLT) ? 3 : 2) k_apply_h_pk(App
   const bool act = (x < nx) && (y < ny);  // nx even: the pair is inside when its first point is
   const i64 col = (i64)wrapi(y, ny) * nx + wrapi(x, nx);
 
-  // halo pair owned by this thread: 2 TYP x-halo pairs, then 2 R rows of TXP pairs
+  // 16-byte chunks this thread copies (nx % 4 == 0, so that a chunk of four
+  // points never straddles the periodic wrap).  Threads 0 .. TYP CH - 1 own
+  // a centre chunk (row cr, points 4 cc ..) of w, w', V - V' and the step's
+  // nonlocal part; the others own the same chunk of V and the nonlocal part,
+  // and the first 2 R CH + 2 TYP of them a halo chunk of w and w' (y halo
+  // rows, then the x halos: columns tx0 - 4 .. tx0 - 1 and tx0 + 32 ..
+  // tx0 + 35).  Points past the grid in a ragged tile are copied from their
+  // periodic images, so that the halo after the last point is in place.
+  const bool cowner = tid < TYP * CH;
+  const int cu = cowner ? tid : tid - TYP * CH;
+  const int cr = cu / CH, cc = cu % CH;
+  const i64 ccol = (i64)wrapi(ty0 + cr, ny) * nx + wrapi(tx0 + 4 * cc, nx);
+  const int csrow = cr + R, cscol = CX0 + 4 * cc;  // shared cell of the chunk in w / w'
   int hrow = -1, hcs = 0;
   i64 hcol = 0;
-  if (tid < 2 * TYP) {
-    const int side = tid / TYP, row = tid % TYP;
-    hrow = row + R;
-    hcs = side == 0 ? 0 : PW + 2;
-    hcol = (i64)wrapi(ty0 + row, ny) * nx + wrapi(side == 0 ? tx0 - 2 : tx0 + PW, nx);
-  } else if (tid < 2 * TYP + 2 * R * TXP) {
-    const int u = tid - 2 * TYP;
-    const int side = u / (R * TXP), r = u % (R * TXP);
-    const int d = r / TXP, c = r % TXP;
-    hrow = side == 0 ? d : TYP + R + d;
-    hcs = 2 + 2 * c;
-    hcol = (i64)wrapi(side == 0 ? ty0 - R + d : ty0 + TYP + d, ny) * nx + wrapi(tx0 + 2 * c, nx);
+  if (!cowner) {
+    if (cu < 2 * R * CH) {
+      const int side = cu / (R * CH), r = cu % (R * CH);
+      const int d = r / CH, c = r % CH;
+      hrow = side == 0 ? d : TYP + R + d;
+      hcs = CX0 + 4 * c;
+      hcol = (i64)wrapi(side == 0 ? ty0 - R + d : ty0 + TYP + d, ny) * nx + wrapi(tx0 + 4 * c, nx);
+    } else if (cu < 2 * R * CH + 2 * TYP) {
+      const int u = cu - 2 * R * CH;
+      const int side = u / TYP, row = u % TYP;
+      hrow = row + R;
+      hcs = side == 0 ? 0 : CX0 + PW;
+      hcol = (i64)wrapi(ty0 + row, ny) * nx + wrapi(side == 0 ? tx0 - 4 : tx0 + PW, nx);
+    }
   }
-  const int cx = 2 + 2 * lx, cy = ly + R;
+  const int cx = CX0 + 2 * lx, cy = ly + R;
 
   const int a_first = z0 - R, a_last = z1 + R;
   int zi = a_first;
@@ -756,18 +777,23 @@ __global__ void __launch_bounds__(NTP, (CUBIC && !NLT) ? 3 : 2) k_apply_h_pk(App
     if (zi < a_last) {
       Stage<R, HIST, NLT>& g = ring[k];
       const i64 zo = (i64)zw * pl;
-      cp_async<8>(&g.w[cy][cx], w + zo + col);
-      if (hrow >= 0) cp_async<8>(&g.w[hrow][hcs], w + zo + hcol);
-      if constexpr (HIST) {
-        cp_async<8>(&g.s[cy][cx], wp + zo + col);
-        if (hrow >= 0) cp_async<8>(&g.s[hrow][hcs], wp + zo + hcol);
-      }
-      if (zi >= z0 && zi < z1) {
-        cp_async<8>(&g.v[ly][2 * lx], V + zo + col);
-        if constexpr (HIST) cp_async<8>(&g.dv[ly][2 * lx], dVp + zo + col);
-        if constexpr (NLT) {
-          cp_async<8>(&g.nl[ly][2 * lx], nlp + zo + col);
-          if constexpr (HIST) cp_async<8>(&g.nls[ly][2 * lx], nlsp + zo + col);
+      const bool cen = zi >= z0 && zi < z1;
+      if (cowner) {
+        cp_async16_cg(&g.w[csrow][cscol], w + zo + ccol);
+        if constexpr (HIST) {
+          cp_async16_cg(&g.s[csrow][cscol], wp + zo + ccol);
+          if (cen) cp_async16_cg(&g.dv[cr][4 * cc], dVp + zo + ccol);
+          if constexpr (NLT)
+            if (cen) cp_async16_cg(&g.nls[cr][4 * cc], nlsp + zo + ccol);
+        }
+      } else {
+        if (cen) {
+          cp_async16_cg(&g.v[cr][4 * cc], V + zo + ccol);
+          if constexpr (NLT) cp_async16_cg(&g.nl[cr][4 * cc], nlp + zo + ccol);
+        }
+        if (hrow >= 0) {
+          cp_async16_cg(&g.w[hrow][hcs], w + zo + hcol);
+          if constexpr (HIST) cp_async16_cg(&g.s[hrow][hcs], wp + zo + hcol);
         }
       }
     }
@@ -797,22 +823,30 @@ __global__ void __launch_bounds__(NTP, (CUBIC && !NLT) ? 3 : 2) k_apply_h_pk(App
       const int pa = base + k;
       if (pa >= a_last) break;
       cp_wait<PFP>();
-      {
-        // plane pa has landed for this thread's own copies: queue its centre
-        // values and convert the cells this thread copied
-        Stage<R, HIST, NLT>& g = ring[k];
-        const float2 wc = lds2(&g.w[cy][cx]);
-        qw[k] = wc;
-        if constexpr (HIST) {
-          const float2 pc = lds2(&g.s[cy][cx]);
-          const float2 sc = sub2(wc, pc);
-          sts2(&g.s[cy][cx], sc);
-          qs[k] = sc;
-          if (hrow >= 0) sts2(&g.s[hrow][hcs], sub2(lds2(&g.w[hrow][hcs]), lds2(&g.s[hrow][hcs])));
-          if (pa >= z0 && pa < z1) sts2(&g.dv[ly][2 * lx], mul2(lds2(&g.dv[ly][2 * lx]), pc));
+      Stage<R, HIST, NLT>& ga = ring[k];
+      if constexpr (HIST) {
+        // plane pa has landed for this thread's own copies: convert the
+        // cells it copied (each pair lane by lane, as one scalar operation)
+        auto conv = [&](int row, int c0) {
+#pragma unroll
+          for (int h = 0; h < 4; h += 2)
+            sts2(&ga.s[row][c0 + h], sub2(lds2(&ga.w[row][c0 + h]), lds2(&ga.s[row][c0 + h])));
+        };
+        if (cowner) {
+          if (pa >= z0 && pa < z1) {
+#pragma unroll
+            for (int h = 0; h < 4; h += 2)
+              sts2(&ga.dv[cr][4 * cc + h], mul2(lds2(&ga.dv[cr][4 * cc + h]), lds2(&ga.s[csrow][cscol + h])));
+          }
+          conv(csrow, cscol);
+        } else if (hrow >= 0) {
+          conv(hrow, hcs);
         }
       }
       __syncthreads();
+      // queue the centre values of plane pa (copied and converted by their owners)
+      qw[k] = lds2(&ga.w[cy][cx]);
+      if constexpr (HIST) qs[k] = lds2(&ga.s[cy][cx]);
       issue_next((k + PFP + 1) % S);
       const int z = pa - R;
       if (z < z0 || !act) continue;
@@ -968,14 +1002,14 @@ enum TileKind { TILE_SCALAR = 0, TILE_PAIR = 1, TILE_PACKED = 2 };
 struct TileShape {
   int kind, tw, th, bx, by;
 };
-static TileShape tile_shape(int nx, int elem_bytes) {
-  if (nx % 2 == 0 && elem_bytes == 4) return {TILE_PACKED, pk::PW, pk::TYP, pk::TXP, pk::TYP};
-  if (nx % 2 == 0) return {TILE_PAIR, PTX, TY, TX, TY};
+static TileShape tile_shape(int nx, int elem_bytes, int align) {
+  if (nx % 4 == 0 && elem_bytes == 4 && align >= 2) return {TILE_PACKED, pk::PW, pk::TYP, pk::TXP, pk::TYP};
+  if (nx % 2 == 0 && align >= 1) return {TILE_PAIR, PTX, TY, TX, TY};
   return {TILE_SCALAR, TX, TY, TX, TY};
 }
 
-int apply_h_ntile(int nx, int ny, int nz, int N, int elem_bytes, int* nzc_out) {
-  const TileShape ts = tile_shape(nx, elem_bytes);
+int apply_h_ntile(int nx, int ny, int nz, int N, int elem_bytes, int* nzc_out, int align) {
+  const TileShape ts = tile_shape(nx, elem_bytes, align);
   const int ntx = (nx + ts.tw - 1) / ts.tw, nty = (ny + ts.th - 1) / ts.th;
   const long long base = (long long)ntx * nty * N;
   int nzc = 1;
@@ -985,13 +1019,31 @@ int apply_h_ntile(int nx, int ny, int nz, int N, int elem_bytes, int* nzc_out) {
   return ntx * nty * nzc;
 }
 
+// Alignment of a launch's blocks (a caller's block need not be aligned):
+// 2 when every block read starts on a 16-byte boundary and the output on a
+// boundary of two elements (the FP32 kernel: 16-byte copies, pair stores);
+// 1 when every block, read or written, starts on a boundary of two elements
+// (the paired kernel copies and stores two elements at a time); 0 otherwise
+// (the scalar kernel: one element per access).
+template <typename T>
+static int block_alignment(const ApplyArgs<T>& a) {
+  auto on = [](const void* q, uintptr_t m) { return reinterpret_cast<uintptr_t>(q) % m == 0; };
+  const void* blk[9] = {a.W[0], a.W[1], a.V[0], a.V[1], a.dV, a.nl, a.nls, a.HW[0], a.HW[1]};
+  for (const void* q : blk)
+    if (!on(q, 2 * sizeof(T))) return 0;
+  for (int k = 0; k < 7; ++k)  // the blocks read
+    if (!on(blk[k], 16)) return 1;
+  return 2;
+}
+
 template <typename T>
 void launch_apply_h(const ApplyArgs<T>& a0, int order, cudaStream_t s, int* ntile_out) {
   ApplyArgs<T> a = a0;
+  const int align = block_alignment(a);
   int nzc = 1;
-  const int ntile = apply_h_ntile(a.nx, a.ny, a.nz, a.N, (int)sizeof(T), &nzc);
+  const int ntile = apply_h_ntile(a.nx, a.ny, a.nz, a.N, (int)sizeof(T), &nzc, align);
   a.nzc = nzc;
-  const TileShape ts = tile_shape(a.nx, (int)sizeof(T));
+  const TileShape ts = tile_shape(a.nx, (int)sizeof(T), align);
   const int ntx = (a.nx + ts.tw - 1) / ts.tw, nty = (a.ny + ts.th - 1) / ts.th;
   dim3 grid(ntx * nty, nzc, a.N), block(ts.bx, ts.by);
   prof_begin("apply_h", s);

@@ -1153,7 +1153,11 @@ static pou_status create_buffers(pou_ctx* c) {
   DALLOC(c->vext, c->ng * sizeof(double));
   CK(cudaMemsetAsync(c->vext, 0, c->ng * sizeof(double), c->stream));
   DALLOC(c->work, c->ng * sizeof(double2));
-  c->ntile = apply_h_ntile(c->nx, c->ny, c->nz, c->N, (int)c->esz, nullptr);
+  // a caller's block that is not aligned takes a kernel with narrower
+  // accesses and another tile shape: room for every layout
+  c->ntile = 0;
+  for (int align = 0; align <= 2; ++align)
+    c->ntile = std::max(c->ntile, apply_h_ntile(c->nx, c->ny, c->nz, c->N, (int)c->esz, nullptr, align));
   DALLOC(c->tilepart, (size_t)c->N * c->ntile * NPT * sizeof(double));
   c->neblk_max = (int)std::max<long long>((long long)num_sms() * 4, (long long)c->nz * c->ny);
   DALLOC(c->epart, (size_t)c->neblk_max * NE * sizeof(double));

@@ -94,7 +94,11 @@ struct ApplyArgs {
 };
 template <typename T>
 void launch_apply_h(const ApplyArgs<T>& a, int order, cudaStream_t s, int* ntile_out);
-int apply_h_ntile(int nx, int ny, int nz, int N, int elem_bytes, int* nzc_out);
+// Tiles of the H-apply launch (the partial-sum layout).  align: 2 when the
+// blocks read are 16-byte aligned and the output 8-byte aligned (the library's
+// own buffers), 1 when only the output is aligned to two elements, 0 otherwise;
+// each level selects the kernel (and tile shape) that its accesses allow.
+int apply_h_ntile(int nx, int ny, int nz, int N, int elem_bytes, int* nzc_out, int align = 2);
 
 // ---------------------------------------------------------------- gram / rotation
 template <typename T>

@@ -521,11 +521,12 @@ def test_evaluate_energy_terms(P, precision, order):
 
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("order,n", [(2, (20, 12, 10)), (4, (20, 12, 10)), (4, (5, 6, 8)), (2, (27, 9, 4)),
-                                     (4, (64, 32, 12)), (2, (32, 48, 5)), (4, (32, 16, 3))])
+                                     (4, (64, 32, 12)), (2, (32, 48, 5)), (4, (32, 16, 3)), (4, (18, 12, 10))])
 def test_apply_h_through_adjoint(P, precision, order, n):
     """a1: HW = -1/2 Lap_h W + V W, read through dE/dU = 2 f dV H U with g = 1/(2 f dV).
-    The grids cover whole and ragged 32 x 16 tiles of the FP32 kernel, odd
-    nx (the scalar kernel) and fewer planes than the stencil's reach in z."""
+    The grids cover whole and ragged 32 x 16 tiles of the FP32 kernel, nx
+    even but not a multiple of 4 (the paired kernel), odd nx (the scalar
+    kernel) and fewer planes than the stencil's reach in z."""
     L, N = (6.0, 5.0, 4.0), 2
     R, Z, U = _system(n, L, N, 9)
     if precision == 1:
@@ -542,6 +543,35 @@ def test_apply_h_through_adjoint(P, precision, order, n):
     ref = O.apply_h(U, O.total_potential(O.density(U), vext, cfg), cfg)
     tol = 1e-11 if precision == 0 else 2e-5
     np.testing.assert_allclose(out.double().cpu().numpy(), ref, atol=tol * np.max(np.abs(ref)))
+    s.close()
+
+
+@pytest.mark.parametrize("offset_in,offset_out", [(1, 0), (0, 1), (1, 1), (2, 2)])
+def test_apply_h_unaligned_caller_blocks(P, offset_in, offset_out):
+    """A caller's FP32 block or output that starts off the 16-byte boundary
+    (a view into a larger buffer) takes a kernel whose accesses it allows;
+    the result is the oracle's either way."""
+    n, L, N, order = (32, 16, 12), (6.0, 5.0, 4.0), 3, 4
+    R, Z, U = _system(n, L, N, 9)
+    U = U.astype(np.float32).astype(np.float64)
+    cfg = ocfg(n, L, N, order=order)
+    s = solver(P, n, L, N, order=order, precision=1)
+    s.set_atoms(R, Z, 0.8)
+    vext = O.vext_gaussians(cfg, R, Z, 0.8)
+    size = U.size
+    bufu = torch.zeros(size + 4, dtype=torch.float32, device="cuda")
+    bufo = torch.zeros(size + 4, dtype=torch.float32, device="cuda")
+    Ud = bufu[offset_in:offset_in + size].view(U.shape)
+    Ud.copy_(dev(U, torch.float32))
+    out = bufo[offset_out:offset_out + size].view(U.shape)
+    g = 1.0 / (2 * O.F_OCC * cfg.dV)
+    s.backward(Ud, g, out)
+    ref = O.apply_h(U, O.total_potential(O.density(U), vext, cfg), cfg)
+    np.testing.assert_allclose(out.double().cpu().numpy(), ref, atol=2e-5 * np.max(np.abs(ref)))
+    # the energy of the same block through the same kernels
+    e = s.evaluate(Ud)
+    refE = O.energy_terms(U, vext, cfg)
+    assert abs(e["kinetic"] - refE.kinetic) <= 2e-6 * abs(refE.kinetic)
     s.close()
 
 
