@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ttt", action="store_true", help="time-to-1e-6 Ha, mixed vs FP64 (long)")
     ap.add_argument("--ttt-max", type=int, default=4000)
+    ap.add_argument("--ttt-ndiag", type=int, default=0,
+                    help="subspace diagonalisation every n steps in the time-to-tolerance runs (Algorithm M; 0: none)")
     ap.add_argument("--ttt-fp64-max", type=int, default=4000, help="cap of the FP64-alone run of --ttt")
     ap.add_argument("--ttt-refine-max", type=int, default=4000, help="cap of the FP64 refinement of --ttt")
     ap.add_argument("--ttt-conv-rel", type=float, default=1e-10,
@@ -289,9 +291,9 @@ def cpu_baseline(workload, steps=2, ns=(8, 16)):
 
 
 # --------------------------------------------------------------- our arm
-def make_solver(pou, w, precision, stream_ptr, bb_variant):
+def make_solver(pou, w, precision, stream_ptr, bb_variant, **kw):
     s = pou.Solver(w.n, w.L, w.N, order=w.order, precision=precision, stream=stream_ptr,
-                   bb_variant=bb_variant)
+                   bb_variant=bb_variant, **kw)
     return s
 
 
@@ -518,7 +520,7 @@ def time_to_tolerance(pou, torch, w, R, Z, U0, stream, args):
         return f
 
     def run(prec, U, max_steps, stop=None):
-        s = make_solver(pou, w, prec, stream.cuda_stream, args.bb_variant)
+        s = make_solver(pou, w, prec, stream.cuda_stream, args.bb_variant, n_diag=args.ttt_ndiag)
         s.set_atoms(R, Z, w.width)
         s.set_orbitals(U)
         torch.cuda.synchronize()
@@ -591,6 +593,7 @@ def time_to_tolerance(pou, torch, w, R, Z, U0, stream, args):
                                 f"{float(E64b[-101] - E64b[-1]) if len(E64b) > 100 else float('nan'):.3g} Ha), "
                                 "and the FP64 form alone")
     res["switch_rule"] = f"mixed energy falls by less than {switch_rel:g} |E| over 100 steps"
+    res["n_diag"] = args.ttt_ndiag
     res["workload"] = w.name
     return res
 

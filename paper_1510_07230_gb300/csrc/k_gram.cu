@@ -687,8 +687,12 @@ void gram_layout(i64 ng, int N, bool general, int* nsplit, int* npair, i64* chun
   const int nsup = (N + ST - 1) / ST;
   const int np = general ? nsup * nsup : nsup * (nsup + 1) / 2;
   const i64 ntiles = (ng + BK - 1) / BK;
-  // one CTA per SM in total (one wave), at least 32 tiles per CTA
+  // one CTA per SM in total (one wave), at least 32 tiles per CTA; the
+  // tensor-core Gram of the FP32 form (symmetric, N > 128) runs a diagonal
+  // pair's two splits in one CTA
   i64 g = std::max(1, num_sms() / np);
+  if (sizeof(T) == 4 && !general && nsup > 1)
+    while (gram_tc_ctas((int)g + 1, nsup) <= num_sms()) ++g;
   g = std::max<i64>(1, std::min<i64>(g, ntiles / 32));
   *npair = np;
   *chunk = ntiles;  // tiles over the whole grid

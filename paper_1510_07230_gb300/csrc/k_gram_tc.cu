@@ -94,7 +94,7 @@ __device__ __forceinline__ void two_sum_into(float& s, float& c, float v) {
 // reduction (the FP64 norm from the H-apply sums), which frees the
 // producers' diagonal registers for the double-float split.
 template <bool VEC, bool TRIAL>
-__global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb) {
+__global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb, int nsplit) {
   extern __shared__ unsigned char smem_raw[];
   if (a.st && a.st->done) return;
   if (!gate_open(a.st, a.gate)) return;
@@ -121,16 +121,42 @@ __global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb)
   const i64 ng = a.ng;
 
   // block pair (I, J) of this CTA and its contiguous range of 32-point
-  // chunks: CTA = split * npair + pair, pairs in upper row-major order
-  const int nsup = (N + 127) / 128, npair = nsup * (nsup + 1) / 2;
-  const int pair = (int)(blockIdx.x % npair);
-  const i64 split = blockIdx.x / npair, G = gridDim.x / npair;
+  // chunks (pairs in upper row-major order).  With one block (N <= 128) CTA
+  // = split.  With several, an off-diagonal pair streams two tiles per chunk
+  // and a diagonal one a single tile, so a diagonal pair takes two splits at
+  // once: every CTA then streams the same number of tiles.  CTAs come in
+  // groups of npair + noff: split 2q for every pair (the diagonal ones
+  // covering splits 2q and 2q + 1, whose slot they fill with zeros), then
+  // split 2q + 1 for the off-diagonal pairs.
+  const int nsup = (N + 127) / 128, npair = nsup * (nsup + 1) / 2, noff = npair - nsup;
+  int pair;
+  i64 split;
+  if (nsup == 1) {
+    pair = 0;
+    split = blockIdx.x;
+  } else {
+    const int q = (int)(blockIdx.x / (npair + noff)), r = (int)(blockIdx.x % (npair + noff));
+    if (r < npair) {
+      pair = r;
+      split = 2 * q;
+    } else {
+      // the (r - npair)-th off-diagonal pair
+      int k = r - npair, Io = 0;
+      for (; k >= nsup - 1 - Io; k -= nsup - 1 - Io, ++Io) {
+      }
+      pair = Io * nsup - Io * (Io - 1) / 2 + 1 + k;
+      split = 2 * q + 1;
+    }
+  }
   int I = 0, J = 0;
   for (int p = pair; p >= nsup - I; p -= nsup - I, ++I) {
   }
   J = I + (pair - (I * nsup - I * (I - 1) / 2));
   const bool offd = I != J;
-  const i64 kb0 = nkb * split / G, kb1 = nkb * (split + 1) / G;
+  const i64 G = nsplit;
+  const i64 split_end = (nsup > 1 && !offd) ? (split + 2 < G ? split + 2 : G) : split + 1;
+  const i64 zslot = (nsup > 1 && !offd && split + 1 < G) ? split + 1 : -1;  // slot this CTA zeroes
+  const i64 kb0 = nkb * split / G, kb1 = nkb * split_end / G;
   // steps: one 128-row tile each; an off-diagonal block takes the I and the
   // J tile of every chunk in turn
   const int nmine = (int)(kb1 - kb0) * (offd ? 2 : 1);
@@ -391,7 +417,8 @@ __global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb)
   // diagonal block at [j][i] (the reduction symmetrises), entry (i, j) of an
   // off-diagonal block (TMEM lane = j) at [i][j]
   const bool bad = *abort_flag != 0;
-  double* out = a.split + (i64)blockIdx.x * (128 * 128);
+  double* out = a.split + (split * npair + pair) * (128 * 128);
+  double* zout = zslot >= 0 ? a.split + (zslot * npair + pair) * (128 * 128) : nullptr;
   if (warp >= EPI0 && warp < MMA_WARP) {
     tc::fence_after_sync();
     const int quad = warp - EPI0;
@@ -411,6 +438,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gram_tc(GramArgs<float> a, i64 nkb)
         if (!offd && col == row) v = diag[row];
         if (bad) v = __longlong_as_double(0x7ff8000000000000ll);
         out[(i64)col * 128 + row] = v;
+        if (zout) zout[(i64)col * 128 + row] = 0.0;
       }
     }
     tc::fence_before_sync();
@@ -434,6 +462,12 @@ bool g_configured = false;
 
 }  // namespace
 
+int gram_tc_ctas(int nsplit, int nsup) {
+  if (nsup == 1) return nsplit;
+  const int npair = nsup * (nsup + 1) / 2, noff = npair - nsup;
+  return nsplit * noff + (nsplit + 1) / 2 * nsup;
+}
+
 bool gram_tc_eligible(const GramArgs<float>& a) {
   return a.B == nullptr && !a.src_cur_pair && a.N >= 1 && a.N <= MAXN;
 }
@@ -452,9 +486,10 @@ void launch_gram_tc(const GramArgs<float>& a, int nsplit, cudaStream_t s) {
   configure_gram_tc();
   const i64 nkb = (a.ng + KB - 1) / KB;
   prof_begin(gram_prof_name(a.trial, a.src_trial_slot, a.src_cur_pair), s);
-  // one CTA per (split, block pair); a CTA without stages writes zeros
-  const int nsup = (a.N + 127) / 128;
-  const int nblk = nsplit * (nsup * (nsup + 1) / 2);
+  // one CTA per (split, block pair), a diagonal pair's CTA covering two
+  // splits when there are several blocks; a CTA without stages writes zeros
+  const int nsup = (a.N + 127) / 128, npair = nsup * (nsup + 1) / 2, noff = npair - nsup;
+  const int nblk = gram_tc_ctas(nsplit, nsup);
   // the source rows of the mode: W[cur] and HW[cur] (trial), W[1 - cur], or A
   bool vec = (a.ng % 4) == 0;
   auto aligned = [](const float* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
@@ -465,13 +500,13 @@ void launch_gram_tc(const GramArgs<float>& a, int nsplit, cudaStream_t s) {
   }
   if (a.trial) {
     if (vec)
-      k_gram_tc<true, true><<<nblk, NTHR, SMEM_BYTES, s>>>(a, nkb);
+      k_gram_tc<true, true><<<nblk, NTHR, SMEM_BYTES, s>>>(a, nkb, nsplit);
     else
-      k_gram_tc<false, true><<<nblk, NTHR, SMEM_BYTES, s>>>(a, nkb);
+      k_gram_tc<false, true><<<nblk, NTHR, SMEM_BYTES, s>>>(a, nkb, nsplit);
   } else if (vec) {
-    k_gram_tc<true, false><<<nblk, NTHR, SMEM_BYTES, s>>>(a, nkb);
+    k_gram_tc<true, false><<<nblk, NTHR, SMEM_BYTES, s>>>(a, nkb, nsplit);
   } else {
-    k_gram_tc<false, false><<<nblk, NTHR, SMEM_BYTES, s>>>(a, nkb);
+    k_gram_tc<false, false><<<nblk, NTHR, SMEM_BYTES, s>>>(a, nkb, nsplit);
   }
   prof_end(s);
 }

@@ -134,6 +134,8 @@ void launch_gram_nsplit(const GramArgs<T>& a, int nsplit, cudaStream_t s);
 // modes only; writes the same [nsplit][128 * 128] split layout (transposed
 // and unsymmetrised: the reduction takes the symmetric part).
 bool gram_tc_eligible(const GramArgs<float>& a);
+// CTAs of a tensor-core Gram launch with nsplit splits over nsup 128-row blocks
+int gram_tc_ctas(int nsplit, int nsup);
 // Bounded-wait self-test (a barrier nothing arrives at): 0 on success with
 // *timed_out = 1 when the wait gave up and recorded it; nonzero on a CUDA error.
 int wait_selftest(double limit_s, int* timed_out);

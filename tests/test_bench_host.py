@@ -59,11 +59,11 @@ class FakeSolver:
 def test_time_to_tolerance_protocol(monkeypatch):
     pou = types.SimpleNamespace(FP64=0, FP32=1)
     torch = types.SimpleNamespace(cuda=types.SimpleNamespace(synchronize=lambda: None))
-    monkeypatch.setattr(bench, "make_solver", lambda pou, w, prec, stream, bb: FakeSolver(prec))
+    monkeypatch.setattr(bench, "make_solver", lambda pou, w, prec, stream, bb, **kw: FakeSolver(prec))
     clock = iter(np.arange(0.0, 1e6, 0.5))  # every perf_counter call advances 0.5 s
     monkeypatch.setattr(bench.time, "perf_counter", lambda: next(clock))
     args = types.SimpleNamespace(ttt_max=6000, ttt_fp64_max=4000, ttt_refine_max=6000, ttt_conv_rel=1e-10,
-                                 bb_variant=3, workload="fake")
+                                 ttt_ndiag=0, bb_variant=3, workload="fake")
     w = types.SimpleNamespace(width=0.8, name="fake")
     res = bench.time_to_tolerance(pou, torch, w, None, None, 0.0, types.SimpleNamespace(cuda_stream=0), args)
     # the mixed form stalls 5e-5 above the minimum: not reached, and it stopped early
