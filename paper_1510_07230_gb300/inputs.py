@@ -51,6 +51,9 @@ WORKLOADS = {
     "l30_g160_n128": Workload("l30_g160_n128", 30.0, 160, 4, 64, "uniform26", 128, 2000, 4),
     # reduced headline system for hardware-counter captures (block > L2, a few GB on the device)
     "l24_g128_n64": Workload("l24_g128_n64", 24.0, 128, 4, 32, "uniform26", 64, 100, 6),
+    # reduced 512-orbital system for hardware-counter captures of the several-block kernels
+    # (block 226 MB > L2, under 3 GB on the device): L=12, 48^3, 13-point, 64 atoms Z~U[2,6], N=512
+    "l12_g48_n512": Workload("l12_g48_n512", 12.0, 48, 4, 64, "uniform26", 512, 20, 7),
     # large: L=40, 192^3, 13-point, 256 atoms Z~U[2,6], N=512, 100 iterations
     "l40_g192_n512": Workload("l40_g192_n512", 40.0, 192, 4, 256, "uniform26", 512, 100, 5),
 }
