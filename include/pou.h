@@ -219,7 +219,10 @@ pou_status pou_get_potential(pou_ctx* ctx, double* V, int on_device);
 pou_status pou_gradient_norm(pou_ctx* ctx, double* out);
 
 /* Energy of an arbitrary block U (not orthonormalised, Eq. energy) without
- * touching the iteration state: builds rho(U), V_H, v_x and the four terms. */
+ * touching the iteration state: builds rho(U), V_H, v_x and the four terms.
+ * A device block of the context's dtype is read in place: it needs only the
+ * element's own alignment (a block off the 16-byte boundary is served by a
+ * kernel with narrower accesses, at some cost in speed). */
 pou_status pou_evaluate(pou_ctx* ctx, const void* U, int dtype, int on_device, pou_energy_terms* out);
 
 /* Adjoint of pou_evaluate: with g = dL/dE,
@@ -229,6 +232,7 @@ pou_status pou_evaluate(pou_ctx* ctx, const void* U, int dtype, int on_device, p
  * per-orbital intermediate is stored.  U == NULL uses the current orbitals.
  * dEdU (same dtype/location as U, or device/host per on_device when U is
  * NULL), dEdR (M*3 host doubles) and dEdZ (M host doubles) may each be NULL.
+ * As for pou_evaluate, device blocks need only element alignment.
  * EINVAL if dEdR/dEdZ are requested without atoms. */
 pou_status pou_backward(pou_ctx* ctx, const void* U, int dtype, int on_device, double g,
                         void* dEdU, double* dEdR, double* dEdZ);
