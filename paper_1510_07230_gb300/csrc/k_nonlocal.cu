@@ -17,8 +17,9 @@
 //   formed from the step, like the local part).  One CTA per (orbital, 32 x
 //   32 tile, run of NL_PLANES z planes): the projectors whose x and y windows
 //   meet the tile are listed once in a fixed order (ballot and prefix counts)
-//   and their column tables staged; on each plane the projectors whose z
-//   window holds it contribute, every thread forming 4 columns of one row.
+//   with their column tables gx and row coefficients gy C, gy (C - C')
+//   staged; on each plane their gz (zero outside the z window) is staged and
+//   every thread forms 4 columns of one row.
 // The H-apply adds NL to H w and NLS to H s; the controller adds the
 // nonlocal energy f sum C_ip^2 to the external term.
 #include "pou_internal.cuh"
