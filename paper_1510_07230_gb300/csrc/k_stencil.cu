@@ -603,11 +603,12 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_apply_h_pair(App
 }
 
 // ----------------------------------------------------------------------------
-// FP32 form with even nx.  Each thread owns two adjacent x points (one
-// float2 per array).  Differences from the paired kernel above, each removing
-// per-point work:
+// FP32 form with nx % 4 == 0 and 16-byte aligned blocks.  Each thread owns
+// two adjacent x points (one float2 per array) for the arithmetic; the planes
+// are copied in 16-byte chunks (four points), each chunk by one thread.
+// Differences from the paired kernel above, each removing per-point work:
 //   * the step s = w - w' is formed once per cell when its plane arrives (each
-//     thread converts the cells it copied itself, before the barrier), so the
+//     thread converts the chunks it copied itself, before the barrier), so the
 //     s-stencil reads s directly; the (V - V') w' term is formed there too and
 //     stored in the V - V' slot;
 //   * the z-neighbours live in circular register queues of the ring's length,
