@@ -54,6 +54,26 @@ def test_invalid_configs_rejected_before_touching_the_device(pou, field, value):
     assert not ctx.value
 
 
+@pytest.mark.parametrize("precision,n_diag,ok", [(1, 0, True), (2, 0, True), (0, 0, False), (1, 10, False),
+                                                 (2, 10, False)])
+def test_more_than_128_orbitals_in_the_fp32_forms_only(pou, precision, n_diag, ok):
+    """N > 128 is accepted by the FP32 forms (split or single TF32 Gram)
+    without the subspace diagonalisation; the validation decides before any
+    device call (without a GPU an accepted configuration fails later, at the
+    device)."""
+    cfg = pou.make_config((16, 16, 18), (6.0, 6.0, 7.0), 512)
+    cfg.precision = precision
+    cfg.n_diag = n_diag
+    ctx = C.c_void_p()
+    st = pou._lib.pou_create(C.byref(cfg), C.byref(ctx))
+    if ok:
+        assert st != pou.EINVAL
+        if ctx.value:
+            pou._lib.pou_destroy(ctx)
+    else:
+        assert st == pou.EINVAL and not ctx.value
+
+
 def test_invalid_grid_rejected(pou):
     for n in [(7, 8, 8), (16, 1, 16), (0, 8, 8)]:  # 7 is not 2^a 3^b 5^c
         cfg = pou.make_config(n, 8.0, 2)
