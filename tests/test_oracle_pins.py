@@ -745,3 +745,39 @@ def test_trial_without_positive_definite_gram_is_refused():
     assert O.try_cholesky_qr(Ud, cfg) is None
     Ud[2] += 1e-9 * U[2]  # numerically singular: pivot ~1e-18 of S_max
     assert O.try_cholesky_qr(Ud, cfg) is None
+
+
+def test_search_directions_are_tangent_gradients():
+    """Sec. 3.1-3.2: OptM-QR's direction Z = HW - W Sigma is the gradient of E
+    on the orthonormality constraint (tangent: <W^T Z> + <Z^T W> = 0; along
+    every tangent direction the derivative of E is 2 f dV sum <z_i, d_i>/dV),
+    and Opt-Par's z_i = H w_i - sigma_ii w_i is the gradient of E in orbital i
+    on its own sphere (<w_i, z_i> = 0; the same derivative along a d_i with
+    <w_i, d_i> = 0).  Derivatives by central finite differences of the energy."""
+    cfg = O.Config(n=(6, 5, 6), L=(4.0, 3.5, 4.5), order=4, N=3)
+    R = np.array([[1.0, 1.2, 2.0], [3.0, 2.5, 0.7]])
+    vext = O.vext_gaussians(cfg, R, np.array([2.0, 4.0]), 0.8)
+    W, _, _ = O.cholesky_qr(inputs.random_orbitals(3, 3, cfg.n), cfg)
+    HW = O.apply_h(W, O.total_potential(O.density(W), vext, cfg), cfg)
+    Zf, _ = O.search_direction(W, HW, cfg, full=True)
+    Zp, sig = O.search_direction(W, HW, cfg)
+    M = O.inner_matrix(W, Zf, cfg)
+    assert np.max(np.abs(M + M.T)) < 1e-12
+    assert np.max(np.abs(np.diag(O.inner_matrix(W, Zp, cfg)))) < 1e-12
+    rng = np.random.default_rng(8)
+    eps = 1e-5
+
+    def dE(D):
+        return (O.energy(W + eps * D, vext, cfg) - O.energy(W - eps * D, vext, cfg)) / (2 * eps)
+
+    for _ in range(4):
+        X = rng.standard_normal(W.shape)
+        # tangent part of X on the constraint <W^T W> = I
+        S = O.inner_matrix(W, X, cfg)
+        D = X - np.einsum("ij,i...->j...", 0.5 * (S + S.T), W)
+        assert abs(dE(D) - 2 * O.F_OCC * cfg.dV * np.sum(Zf * D)) <= 1e-7 * max(1.0, abs(dE(D)))
+        # one orbital on its own sphere
+        i = int(rng.integers(0, 3))
+        Di = np.zeros_like(W)
+        Di[i] = X[i] - cfg.dV * np.sum(W[i] * X[i]) * W[i]
+        assert abs(dE(Di) - 2 * O.F_OCC * cfg.dV * np.sum(Zp[i] * Di[i])) <= 1e-7 * max(1.0, abs(dE(Di)))
