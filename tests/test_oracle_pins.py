@@ -781,3 +781,23 @@ def test_search_directions_are_tangent_gradients():
         Di = np.zeros_like(W)
         Di[i] = X[i] - cfg.dV * np.sum(W[i] * X[i]) * W[i]
         assert abs(dE(Di) - 2 * O.F_OCC * cfg.dV * np.sum(Zp[i] * Di[i])) <= 1e-7 * max(1.0, abs(dE(Di)))
+
+
+def test_energy_criterion_stops_at_the_first_qualifying_step():
+    """Sec. 4.2's stopping rule on a real trajectory: df^l is the change of
+    the energy relative to |E^(l-1)| + 1, and the run stops at the first l
+    whose average of df^l, df^(l-1), df^(l-2) is below the tolerance."""
+    cfg = O.cubic(10, 7.0, order=2, N=4)
+    R, Z = inputs.atoms(33, 2, 7.0, "const4")
+    vext = O.vext_gaussians(cfg, R, Z, 0.8)
+    U0 = inputs.random_orbitals(33, 4, cfg.n)
+    E0 = O.initial_state(U0, vext, cfg).E
+    free = O.run(U0, vext, cfg, 150)
+    E = np.array([E0] + [h.energy for h in free.history])
+    df = np.abs(np.diff(E)) / (np.abs(E[:-1]) + 1.0)
+    avg = (df[2:] + df[1:-1] + df[:-2]) / 3.0
+    tol = float(np.sort(avg)[len(avg) // 2])  # a tolerance met part way through
+    first = int(np.nonzero(avg < tol)[0][0]) + 3  # steps taken when it is first met
+    st = O.run(U0, vext, cfg, 150, e_tol=tol)
+    assert st.l == first
+    np.testing.assert_allclose(st.df, df[:first], rtol=0, atol=0)
